@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for ordinary kriging of missing inter-slice voxels (arXiv 2303.09523).
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain reference the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import it.  It shares no code with
+the CUDA library (``paper_2303_09523_gb300``) and neither imports the other.
+
+The arithmetic lives in ``krig_oracle.c`` (Gaussian elimination with partial
+pivoting on the bordered ordinary-kriging system, Appendix A with one constant
+predictor; sub-block layout of Algorithm 1).  This module only marshals numpy
+arrays through ctypes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPHERICAL, EXPONENTIAL, LINEAR = 0, 1, 2
+_MODELS = {"spherical": SPHERICAL, "exponential": EXPONENTIAL, "linear": LINEAR}
+
+
+class _Vg(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("pad", ctypes.c_int32), ("nugget", ctypes.c_double),
+                ("sill", ctypes.c_double), ("range", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        vp = ctypes.POINTER(_Vg)
+        i32 = ctypes.c_int32
+        lib.orc_gamma.argtypes = [vp, ctypes.c_double]
+        lib.orc_gamma.restype = ctypes.c_double
+        lib.orc_gamma_grad.argtypes = [vp, ctypes.c_double, dp]
+        lib.orc_gamma_grad.restype = None
+        lib.orc_gauss_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
+        lib.orc_ok_solve.argtypes = [ctypes.c_int, dp, dp, vp, dp, dp, dp, dp, dp, dp, dp]
+        lib.orc_krige_volume.argtypes = [dp, i32, i32, i32, i32, i32, i32, vp, i32, dp, dp]
+        lib.orc_krige_voxels.argtypes = [dp, i32, i32, i32, i32, i32, vp, ctypes.c_int64, i64p, i32, dp, dp]
+        lib.orc_loo.argtypes = [dp, i32, i32, i32, i32, i32, vp, i32, dp, dp, dp, dp]
+        lib.orc_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _vg(model="spherical", nugget=0.0, sill=1.0, range=8.0):
+    m = _MODELS[model] if isinstance(model, str) else int(model)
+    return _Vg(m, 0, float(nugget), float(sill), float(range))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(st, what):
+    if st != 0:
+        raise OracleError("%s failed with status %d" % (what, st))
+
+
+def max_threads() -> int:
+    return _load().orc_max_threads()
+
+
+def gamma(h, **vg) -> float:
+    """Semivariogram value at lag ``h`` (gamma(0) = 0)."""
+    v = _vg(**vg)
+    return _load().orc_gamma(ctypes.byref(v), float(h))
+
+
+def gamma_grad(h, **vg) -> np.ndarray:
+    v = _vg(**vg)
+    d = np.zeros(3)
+    _load().orc_gamma_grad(ctypes.byref(v), float(h), _ptr(d))
+    return d
+
+
+def gauss_solve(A, B):
+    """The oracle's own Gaussian elimination with partial pivoting."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    B = np.array(B, dtype=np.float64, order="C", copy=True)
+    squeeze = B.ndim == 1
+    if squeeze:
+        B = B[:, None].copy()
+    m, nrhs = B.shape
+    _check(_load().orc_gauss_solve(m, _ptr(A), _ptr(B), nrhs), "gauss_solve")
+    return B[:, 0] if squeeze else B
+
+
+def ok_solve(points, s0, values=None, grad=False, **vg):
+    """Ordinary kriging at ``s0`` from ``points`` (K x 3).
+
+    Returns dict with ``w`` (K), ``mu``, ``var``, ``est`` (if values given) and,
+    with ``grad=True``, ``dw`` (K x 3) and ``dvar`` (3) w.r.t. (nugget, sill, range).
+    """
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    K = pts.shape[0]
+    s0 = np.ascontiguousarray(s0, dtype=np.float64)
+    vals = None if values is None else np.ascontiguousarray(values, dtype=np.float64)
+    w = np.zeros(K)
+    mu = np.zeros(1)
+    var = np.zeros(1)
+    est = np.zeros(1)
+    dw = np.zeros((K, 3)) if grad else None
+    dvar = np.zeros(3) if grad else None
+    v = _vg(**vg)
+    st = _load().orc_ok_solve(K, _ptr(pts), _ptr(s0), ctypes.byref(v), _ptr(vals), _ptr(w), _ptr(mu),
+                              _ptr(var), _ptr(est), _ptr(dw), _ptr(dvar))
+    _check(st, "ok_solve")
+    out = {"w": w, "mu": float(mu[0]), "var": float(var[0])}
+    if vals is not None:
+        out["est"] = float(est[0])
+    if grad:
+        out["dw"] = dw
+        out["dvar"] = dvar
+    return out
+
+
+def n_out(n, g):
+    return (n - 1) * g + 1
+
+
+def krige_volume(slices, g, r, k_sub=1, threads=0, want_var=True, **vg):
+    """Whole-volume kriging (Algorithm 1 steps 2-4, merged as in Sec. 4.2).
+
+    ``slices``: (n, H, W) array, converted to float64.  Returns (out, var),
+    each ((n-1)g+1, H, W) float64; ``var`` is None if ``want_var`` is False.
+    """
+    s = np.ascontiguousarray(slices, dtype=np.float64)
+    n, H, W = s.shape
+    out = np.empty((n_out(n, g), H, W))
+    var = np.empty_like(out) if want_var else None
+    v = _vg(**vg)
+    st = _load().orc_krige_volume(_ptr(s), n, H, W, g, r, k_sub, ctypes.byref(v), threads, _ptr(out), _ptr(var))
+    _check(st, "krige_volume")
+    return out, var
+
+
+def krige_voxels(slices, g, r, zyx, threads=0, **vg):
+    """Estimate and variance at selected output voxels ``zyx`` (M x 3, output z)."""
+    s = np.ascontiguousarray(slices, dtype=np.float64)
+    n, H, W = s.shape
+    idx = np.ascontiguousarray(zyx, dtype=np.int64).reshape(-1, 3)
+    est = np.empty(idx.shape[0])
+    var = np.empty(idx.shape[0])
+    v = _vg(**vg)
+    st = _load().orc_krige_voxels(_ptr(s), n, H, W, g, r, ctypes.byref(v), idx.shape[0],
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), threads, _ptr(est), _ptr(var))
+    _check(st, "krige_voxels")
+    return est, var
+
+
+def loo(slices, g, r, threads=0, want_pred=False, want_grad_theta=False, want_grad_slices=False, **vg):
+    """Leave-one-slice-out CV loss; optional predictions and gradients.
+
+    Returns dict: ``loss``, and ``pred`` ((n-2), H, W), ``grad_theta`` (3:
+    nugget, sill, range), ``grad_slices`` (n, H, W) when requested.
+    """
+    s = np.ascontiguousarray(slices, dtype=np.float64)
+    n, H, W = s.shape
+    loss = np.zeros(1)
+    pred = np.empty((n - 2, H, W)) if want_pred else None
+    gt = np.zeros(3) if want_grad_theta else None
+    gs = np.zeros((n, H, W)) if want_grad_slices else None
+    v = _vg(**vg)
+    st = _load().orc_loo(_ptr(s), n, H, W, g, r, ctypes.byref(v), threads, _ptr(loss), _ptr(pred), _ptr(gt), _ptr(gs))
+    _check(st, "loo")
+    out = {"loss": float(loss[0])}
+    if want_pred:
+        out["pred"] = pred
+    if want_grad_theta:
+        out["grad_theta"] = gt
+    if want_grad_slices:
+        out["grad_slices"] = gs
+    return out
