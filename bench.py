@@ -1,0 +1,356 @@
+"""Benchmark: kriged (interpolated) voxels per second on one GB300.
+
+One step = one pass of the kriging path over one synthetic slice stack: the
+geometry-class solve and the stencil apply of the DS form (sub-block
+partition and class enumeration are planned once, on the host).  The headline
+workload is the spine-like stack: 24 known 256x256 uint16 slices, Z factor 4
+(93 output slices), 4 Z sub-blocks, 18-point window, spherical variogram.
+
+Prints one JSON line (rank 0).  See ``--help`` for options.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kriged voxels/s on 1 GB300, mixed/batched vs plain FP64 at stated err; fwd+bwd vox/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
+# profiles/ (None until captured, and again whenever the kernel changes).
+NCU_TRAFFIC = {
+    "spine": None,
+    "brain": None,
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name):
+    from paper_2303_09523_gb300 import phantoms
+    if name == "spine":
+        return phantoms.spine()
+    if name == "brain":
+        return phantoms.brain()
+    if name == "tiny":
+        return phantoms.tiny_ellipsoids()
+    raise SystemExit("unknown workload %s" % name)
+
+
+def algorithmic_bytes(vol):
+    """Bytes a launch of the stencil must move: read every known slice once, write every output slice once."""
+    esz_in = vol.slices.dtype.itemsize
+    esz_out = 8 if vol.slices.dtype == np.float64 else 4
+    return vol.n * vol.H * vol.W * esz_in + vol.n_out * vol.H * vol.W * esz_out
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(vol, target_s=12.0, threads=0, seed=0):
+    """Time the FP64 oracle on a bounded random sample of missing voxels of the workload."""
+    import oracle
+    vals = vol.values_f64()
+    g = vol.zfactor
+    rng = np.random.default_rng(seed)
+
+    def sample(count):
+        j = rng.integers(0, vol.n - 1, count)
+        t = rng.integers(1, g, count)
+        return np.stack([j * g + t, rng.integers(0, vol.H, count), rng.integers(0, vol.W, count)], 1)
+
+    probe = sample(2000 if threads != 1 else 300)
+    t0 = time.perf_counter()
+    oracle.krige_voxels(vals, g, vol.half_w, probe, threads=threads, **vol.variogram())
+    dt = time.perf_counter() - t0
+    count = int(max(1000, min(5_000_000, len(probe) * target_s / max(dt, 1e-6))))
+    idx = sample(count)
+    t0 = time.perf_counter()
+    oracle.krige_voxels(vals, g, vol.half_w, idx, threads=threads, **vol.variogram())
+    dt = time.perf_counter() - t0
+    used = threads if threads > 0 else oracle.max_threads()
+    return count / dt, count, dt, used
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step krige a bounded random sample of the workload."""
+    if rank != 0:
+        return
+    vol = workload(args.workload)
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(vol, target_s=args.ref_step_s / 4)
+    t_all = 0.0
+    vox = 0
+    for s in range(args.steps):
+        rate, count, dt, used = cpu_oracle_rate(vol, target_s=args.ref_step_s, seed=s + 1)
+        rates.append(rate)
+        t_all += dt
+        vox += count
+    value = vox / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": vol.name, "form": "oracle FP64 per voxel (Gaussian elimination)"},
+        "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": used, "kind": "oracle",
+                         "sample": "%d random missing voxels per step of %s" % (vox // args.steps, vol.name)},
+        "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="spine", choices=["spine", "brain", "tiny"])
+    ap.add_argument("--forms-steps", type=int, default=3, help="steps for the per-voxel forms comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip form comparison and at-scale lines")
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mine":
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2303_09523_gb300 import binding
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl", device_id=dev)
+        dist = dist_
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    vol = workload(args.workload)
+    s_host = torch.from_numpy(np.ascontiguousarray(vol.slices))
+    s_dev = s_host.to(dev)
+    code = binding.dtype_code(s_dev.dtype)
+    desc = binding.desc_for(tuple(s_dev.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks, code, vol.in_scale)
+    out_dt = binding.out_dtype(code)
+    out = torch.empty((vol.n_out, vol.H, vol.W), dtype=out_dt, device=dev)
+    params = binding.variogram_tensor([vol.variogram()], device=dev)
+    plan = binding.Plan([desc], form="DS", device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.interpolate([s_dev], [out], params, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    plan.device_status(stream)
+
+    # ---------------- timed region (device time, L2 flushed before every step)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    plan.set_timing(True)
+    plan.get_timing()
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    plan.set_timing(False)
+    kms, klaunch = plan.get_timing()
+    plan.device_status(stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    vox_step = vol.n_missing
+    value = vox_step * args.steps * world / (total_ms * 1e-3)
+
+    # dominant kernel (stencil apply) roofline
+    peak, peak_kind = _peaks()
+    apply_ms = kms[1] / max(klaunch[1], 1)
+    solve_ms = kms[0] / max(klaunch[0], 1)
+    abytes = algorithmic_bytes(vol)
+    achieved = abytes / (apply_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get(args.workload), "kernel": "k_ds_apply",
+                "algorithmic_bytes": abytes, "avg_launch_ms": apply_ms, "peak_source": peak_kind + " hbm_gbs",
+                "class_solve_avg_ms": solve_ms}
+
+    # ---------------- end to end through the public API with host buffers
+    s_pin = s_host.pin_memory()
+    out_pin = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    s_stage = torch.empty_like(s_dev)
+
+    def e2e_step():
+        s_stage.copy_(s_pin, non_blocking=True)
+        plan.interpolate([s_stage], [out], params, None, stream)
+        out_pin.copy_(out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": vox_step * args.steps * world / (e2e_ms * 1e-3), "unit": "voxels/s",
+           "h2d_bytes_per_step": int(s_pin.numel() * s_pin.element_size()),
+           "d2h_bytes_per_step": int(out_pin.numel() * out_pin.element_size())}
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = compare_forms(args, vol, s_dev, desc, params, out, dev, stream)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        rate, count, dt, used = cpu_oracle_rate(vol, target_s=12.0)
+        rate1, count1, dt1, _ = cpu_oracle_rate(vol, target_s=4.0, threads=1)
+        cpu = {"value": rate, "unit": "voxels/s", "cores": used, "kind": "oracle",
+               "sample": "%d random missing voxels of %s (%.1f s); single-core: %.4g voxels/s on %d voxels"
+                         % (count, vol.name, dt, rate1, count1)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 stencil / f64-refined f32 solve",
+            "data": "synthetic",
+            "config": {"workload": vol.name, "form": "DS", "n_known": vol.n, "H": vol.H, "W": vol.W,
+                       "zfactor": vol.zfactor, "half_w": vol.half_w, "n_sub_blocks": vol.n_sub_blocks,
+                       "variogram": vol.variogram(), "interpolated_voxels_per_step": vox_step,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(sum(klaunch)),
+            "clocks": clk.summary(),
+            "wall_s_timed_region": t_wall,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def compare_forms(args, vol, s_dev, desc, params, out_ds, dev, stream):
+    """Plain FP64 per-voxel form (P64) and the mixed per-voxel form (PMX) on the same workload."""
+    import torch
+    from paper_2303_09523_gb300 import binding
+    res = {}
+    ref = None
+    for form in ("P64", "PMX"):
+        plan = binding.Plan([desc], form=form, device=dev)
+        o = torch.empty_like(out_ds)
+        plan.interpolate([s_dev], [o], params, None, stream)
+        plan.device_status(stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.forms_steps):
+            plan.interpolate([s_dev], [o], params, None, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.forms_steps
+        res[form] = {"value": vol.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms}
+        if form == "P64":
+            ref = o.double()
+        else:
+            res[form]["max_rel_err_vs_P64"] = float((o.double() - ref).abs().max() / ref.abs().max())
+        plan.close()
+    res["DS_max_rel_err_vs_P64"] = float((out_ds.double() - ref).abs().max() / ref.abs().max())
+    return {"forms": res}
+
+
+if __name__ == "__main__":
+    main()

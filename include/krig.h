@@ -1,0 +1,168 @@
+/*
+ * krig.h -- C ABI of the GB300 kriging library (libkrig.so).
+ *
+ * Ordinary kriging of the missing inter-slice voxels of registered 2-D slice
+ * stacks, after arXiv 2303.09523 ("Fast 3D Volumetric Image Reconstruction
+ * from 2D MRI Slices by Parallel Processing"):
+ *   - Algorithm 1 (input: n slices, the inter-slice gap, k): the stack is cut
+ *     along Z into k sub-blocks of whole gaps, each block is filled, and the
+ *     blocks are merged at their stored offsets (Sec. 4.2);
+ *   - Sec. 4.1.2: every missing voxel is a weighted linear sum of known voxels
+ *     in 3-D, with weights that minimise the estimation variance subject to
+ *     unbiasedness;
+ *   - Appendix A: the weights and the Lagrange multiplier solve the extended
+ *     system; with one constant predictor this is ordinary kriging.
+ *
+ * Geometry.  A volume has n known slices of H x W pixels (x fastest) and a
+ * Z-upsampling factor g.  The output has (n-1)g+1 slices; known slice j is
+ * output slice j*g and is copied through bit-exactly.  The missing voxel
+ * (x, y, j*g+t), 1 <= t < g, is estimated from the (2r+1)x(2r+1) in-plane
+ * window around (x, y) in known slices j and j+1 (K = 2(2r+1)^2 points),
+ * truncated at the in-plane border.  Distances are Euclidean in output-voxel
+ * units (in-plane spacing 1, known slices g apart).
+ *
+ * Variogram (semivariogram, gamma(0) = 0; `sill` is the partial sill):
+ *   spherical:   nugget + sill (1.5 h/a - 0.5 (h/a)^3) for h < a, else nugget + sill
+ *   exponential: nugget + sill (1 - exp(-3h/a))
+ *
+ * Conventions for every entry point:
+ *   - All slice, output and parameter buffers are caller-owned DEVICE memory
+ *     unless stated.  The plan owns host metadata only; device scratch lives
+ *     in a caller-owned workspace (krig_plan_set_workspace).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  Argument errors are returned
+ *     before anything is enqueued.  Errors found on the device (a singular
+ *     system, a timed-out wait) are sticky bits read by
+ *     krig_plan_device_status.
+ *   - No C++ exception crosses this boundary.  krig_last_error() gives a
+ *     thread-local message for the last non-OK status of this thread.
+ *   - Calls that share one plan (and so one workspace) must not overlap on
+ *     the device: enqueue them on one stream or synchronise between them.
+ */
+#ifndef KRIG_H
+#define KRIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct krig_plan_s* krig_plan_t;
+
+typedef enum {
+    KRIG_OK = 0,
+    KRIG_EINVAL = 1,        /* bad argument (null pointer, size out of range, ...) */
+    KRIG_ENOMEM = 2,        /* host allocation failed */
+    KRIG_ECUDA = 3,         /* a CUDA runtime call failed */
+    KRIG_ESINGULAR = 4,     /* a kriging system was singular (e.g. nugget = sill = 0) */
+    KRIG_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    KRIG_EWORKSPACE = 6,    /* no workspace, or one that is too small or misaligned */
+    KRIG_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} krig_status;
+
+typedef enum { KRIG_SPHERICAL = 0, KRIG_EXPONENTIAL = 1 } krig_model;
+
+/* Storage type of the known slices.  Output type: float64 for KRIG_F64
+ * input, float32 otherwise.  KRIG_U16 values are float32(u) * in_scale
+ * (float32 multiply). */
+typedef enum { KRIG_F64 = 0, KRIG_F32 = 1, KRIG_U16 = 2 } krig_dtype;
+
+/* How the kriging systems are solved.
+ *   P64: one FP64 system per missing voxel (the plain reference form).
+ *   PMX: one system per missing voxel, FP32 factorisation plus one FP64
+ *        iterative-refinement step.
+ *   DS : one FP64 system per neighbourhood geometry class, applied to every
+ *        voxel of that class as an FP32 stencil (FP64 for KRIG_F64 input).
+ *        A voxel's system depends only on t and on how its window is
+ *        truncated at the border, so the solutions repeat across voxels. */
+typedef enum { KRIG_FORM_P64 = 0, KRIG_FORM_PMX = 1, KRIG_FORM_DS = 2 } krig_form;
+
+/* One slice stack.  Limits: H, W in [1, 65536]; 2 <= n_known <= 65536;
+ * 1 <= zfactor <= 8; 1 <= n_sub_blocks <= n_known - 1; half_w in {0, 1, 2}. */
+typedef struct {
+    int32_t H, W;
+    int32_t n_known;       /* n */
+    int32_t zfactor;       /* g */
+    int32_t n_sub_blocks;  /* k: Z sub-blocks of whole gaps (Algorithm 1, step 2) */
+    int32_t half_w;        /* r: window (2r+1)^2 per bracketing slice */
+    int32_t in_dtype;      /* krig_dtype */
+    float in_scale;        /* KRIG_U16 only; ignored otherwise */
+} krig_volume_desc;
+
+/* Variogram parameters, one per volume, in DEVICE memory for the calls below
+ * (so a captured CUDA graph can be replayed with new values). 32 bytes. */
+typedef struct {
+    int32_t model;   /* krig_model */
+    int32_t pad;
+    double nugget;   /* >= 0 */
+    double sill;     /* partial sill, >= 0; nugget + sill > 0 */
+    double range;    /* a > 0, in output-voxel units */
+} krig_variogram;
+
+/* Plan flags.
+ *   KRIG_FLAG_DS_FP64_SOLVE: DS form only -- factorise the class systems in
+ *   FP64 instead of FP32 followed by one FP64 iterative-refinement step. */
+#define KRIG_FLAG_DS_FP64_SOLVE 0x1u
+
+#define KRIG_MAX_VOLUMES 64
+
+/* Create a plan for n_vols volumes (1..KRIG_MAX_VOLUMES) solved in `form`.
+ * Validates the descriptors, partitions each stack into its Z sub-blocks and
+ * in-plane tiles, enumerates the geometry classes and sizes the workspace.
+ * *plan receives the handle (NULL on error); *workspace_bytes_out (nullable)
+ * the device workspace size that krig_plan_set_workspace needs.  Does not
+ * touch the GPU.  Errors: KRIG_EINVAL, KRIG_EUNSUPPORTED, KRIG_ENOMEM. */
+krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, int32_t n_vols,
+                             krig_form form, uint32_t flags, size_t* workspace_bytes_out);
+
+/* Attach caller-owned device memory (>= the size reported above, 256-byte
+ * aligned) as the plan's workspace and upload the plan's tables into it
+ * (synchronous: returns after the upload, on the current device).  The
+ * memory must stay valid until the plan is destroyed or another workspace
+ * is set.  Errors: KRIG_EWORKSPACE, KRIG_ECUDA. */
+krig_status krig_plan_set_workspace(krig_plan_t plan, void* d_workspace, size_t bytes);
+
+/* Interpolate every volume (Algorithm 1 steps 2-4, Sec. 4.1.2, Appendix A).
+ *   d_slices[v]: device, n x H x W of the volume's in_dtype (16-byte aligned).
+ *   d_out[v]:    device, ((n-1)g+1) x H x W, float64 for KRIG_F64 input else
+ *                float32 (16-byte aligned).  Known slices are copied through.
+ *   d_var:       nullable host array of n_vols nullable device pointers, each
+ *                ((n-1)g+1) x H x W float32: the kriging variance
+ *                w^T gamma0 + mu of every voxel (0 at known slices).
+ *   d_params:    device array of n_vols krig_variogram.
+ * The host arrays d_slices / d_out / d_var are read during the call only.
+ * Errors: KRIG_EINVAL, KRIG_EWORKSPACE, KRIG_ECUDA (launch). */
+krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void* const* d_out,
+                             float* const* d_var, const krig_variogram* d_params, void* stream);
+
+/* Wait for the stream, then return and clear the plan's device error bits:
+ * KRIG_OK, KRIG_ESINGULAR or KRIG_ETIMEOUT (the first set, in that order). */
+krig_status krig_plan_device_status(krig_plan_t plan, void* stream);
+
+/* Kernel timing (tracing).  While enabled, each launch of the plan is
+ * bracketed by CUDA events on the call's stream; krig_plan_get_timing waits
+ * for them and returns the summed milliseconds per kernel kind and the number
+ * of launches, then resets the sums.  kinds: 0 class/voxel solve, 1 stencil
+ * apply (DS), 2 loo forward, 3 backward.  Arrays have KRIG_TIMING_KINDS
+ * entries (nullable). */
+#define KRIG_TIMING_KINDS 4
+krig_status krig_plan_set_timing(krig_plan_t plan, int32_t enable);
+krig_status krig_plan_get_timing(krig_plan_t plan, double* ms_out, int64_t* launches_out);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char* krig_last_error(void);
+
+/* Destroy the plan (host memory only; the workspace stays the caller's).
+ * NULL is ignored. */
+void krig_plan_destroy(krig_plan_t plan);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t krig_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRIG_H */

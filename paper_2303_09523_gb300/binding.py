@@ -1,0 +1,218 @@
+"""Thin ctypes binding over ``libkrig.so`` (C ABI in ``include/krig.h``).
+
+Argument marshalling only: every step of the kriging path runs in the
+library's CUDA kernels.  PyTorch supplies device memory (the workspace and the
+caller's tensors) and the CUDA stream.  There is no fallback: if the library
+is missing, ``lib()`` raises.
+"""
+import ctypes
+import os
+import struct
+
+from . import build as _build
+
+KRIG_OK, KRIG_EINVAL, KRIG_ENOMEM, KRIG_ECUDA, KRIG_ESINGULAR, KRIG_ETIMEOUT, KRIG_EWORKSPACE, KRIG_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["KRIG_OK", "KRIG_EINVAL", "KRIG_ENOMEM", "KRIG_ECUDA", "KRIG_ESINGULAR", "KRIG_ETIMEOUT",
+                "KRIG_EWORKSPACE", "KRIG_EUNSUPPORTED"]
+SPHERICAL, EXPONENTIAL = 0, 1
+F64, F32, U16 = 0, 1, 2
+FORM_P64, FORM_PMX, FORM_DS = 0, 1, 2
+FORMS = {"P64": FORM_P64, "PMX": FORM_PMX, "DS": FORM_DS}
+MODELS = {"spherical": SPHERICAL, "exponential": EXPONENTIAL}
+FLAG_DS_FP64_SOLVE = 0x1
+MAX_VOLUMES = 64
+TIMING_KINDS = 4
+
+
+class VolumeDesc(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("n_known", ctypes.c_int32),
+                ("zfactor", ctypes.c_int32), ("n_sub_blocks", ctypes.c_int32), ("half_w", ctypes.c_int32),
+                ("in_dtype", ctypes.c_int32), ("in_scale", ctypes.c_float)]
+
+
+class Variogram(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("pad", ctypes.c_int32), ("nugget", ctypes.c_double),
+                ("sill", ctypes.c_double), ("range", ctypes.c_double)]
+
+
+class KrigError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libkrig.so.  Raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libkrig.so is not built (%s); run __graft_entry__.build()" % path)
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    L.krig_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(VolumeDesc), ctypes.c_int32, ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]
+    L.krig_plan_create.restype = ctypes.c_int
+    L.krig_plan_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.krig_plan_set_workspace.restype = ctypes.c_int
+    L.krig_interpolate.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+    L.krig_interpolate.restype = ctypes.c_int
+    L.krig_plan_device_status.argtypes = [vp, vp]
+    L.krig_plan_device_status.restype = ctypes.c_int
+    L.krig_plan_set_timing.argtypes = [vp, ctypes.c_int32]
+    L.krig_plan_set_timing.restype = ctypes.c_int
+    L.krig_plan_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.krig_plan_get_timing.restype = ctypes.c_int
+    L.krig_last_error.argtypes = []
+    L.krig_last_error.restype = ctypes.c_char_p
+    L.krig_plan_destroy.argtypes = [vp]
+    L.krig_plan_destroy.restype = None
+    L.krig_version.argtypes = []
+    L.krig_version.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != KRIG_OK:
+        raise KrigError(st, lib().krig_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dtype_code(torch_dtype):
+    import torch
+    return {torch.float64: F64, torch.float32: F32, torch.uint16: U16}[torch_dtype]
+
+
+def variogram_bytes(params) -> bytes:
+    """Pack a list of dicts (model, nugget, sill, range) as krig_variogram structs."""
+    out = b""
+    for p in params:
+        m = p["model"]
+        m = MODELS[m] if isinstance(m, str) else int(m)
+        out += struct.pack("<iiddd", m, 0, float(p["nugget"]), float(p["sill"]), float(p["range"]))
+    return out
+
+
+def variogram_tensor(params, device="cuda"):
+    """Device buffer of krig_variogram structs (uint8 tensor, 32 bytes per volume)."""
+    import torch
+    raw = variogram_bytes(params)
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+class Plan:
+    """A kriging plan over one or more volumes, with a torch-allocated workspace."""
+
+    def __init__(self, descs, form="DS", flags=0, device=None, workspace=True):
+        L = lib()
+        self._lib = L
+        n = len(descs)
+        arr = (VolumeDesc * n)()
+        for i, d in enumerate(descs):
+            arr[i] = VolumeDesc(int(d["H"]), int(d["W"]), int(d["n_known"]), int(d["zfactor"]),
+                                int(d["n_sub_blocks"]), int(d["half_w"]), int(d["in_dtype"]),
+                                float(d.get("in_scale", 1.0)))
+        self.descs = [dict(d) for d in descs]
+        self.form = FORMS[form] if isinstance(form, str) else int(form)
+        h = ctypes.c_void_p()
+        nbytes = ctypes.c_size_t()
+        _check(L.krig_plan_create(ctypes.byref(h), arr, n, self.form, flags, ctypes.byref(nbytes)))
+        self.handle = h
+        self.workspace_bytes = nbytes.value
+        self.workspace = None
+        if workspace:
+            import torch
+            dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=dev)
+            _check(L.krig_plan_set_workspace(h, _ptr(self.workspace), self.workspace_bytes))
+
+    def interpolate(self, slices, outs, params, variances=None, stream=None):
+        n = len(self.descs)
+        S = (ctypes.c_void_p * n)(*[t.data_ptr() for t in slices])
+        O = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+        V = None
+        if variances is not None:
+            V = (ctypes.c_void_p * n)(*[(0 if t is None else t.data_ptr()) for t in variances])
+        _check(self._lib.krig_interpolate(self.handle, S, O, V, _ptr(params), _stream(stream)))
+
+    def device_status(self, stream=None):
+        _check(self._lib.krig_plan_device_status(self.handle, _stream(stream)))
+
+    def set_timing(self, enable=True):
+        _check(self._lib.krig_plan_set_timing(self.handle, 1 if enable else 0))
+
+    def get_timing(self):
+        ms = (ctypes.c_double * TIMING_KINDS)()
+        cnt = (ctypes.c_int64 * TIMING_KINDS)()
+        _check(self._lib.krig_plan_get_timing(self.handle, ms, cnt))
+        return list(ms), list(cnt)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.krig_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def desc_for(slices_shape, zfactor, half_w, n_sub_blocks, dtype_code_, in_scale=1.0):
+    n, H, W = slices_shape
+    return dict(H=H, W=W, n_known=n, zfactor=zfactor, n_sub_blocks=n_sub_blocks, half_w=half_w,
+                in_dtype=dtype_code_, in_scale=in_scale)
+
+
+def out_dtype(dtype_code_):
+    import torch
+    return torch.float64 if dtype_code_ == F64 else torch.float32
+
+
+def krige(volumes, form="DS", want_var=False, flags=0, stream=None):
+    """Interpolate a list of volumes in one call.
+
+    ``volumes``: list of dicts with ``slices`` (CUDA tensor, n x H x W of
+    float64 / float32 / uint16), ``zfactor``, ``half_w``, ``n_sub_blocks``,
+    ``variogram`` (dict) and, for uint16, ``in_scale``.  Returns (outs, vars).
+    """
+    import torch
+    descs, outs, vars_, params = [], [], [], []
+    for v in volumes:
+        s = v["slices"]
+        code = dtype_code(s.dtype)
+        d = desc_for(tuple(s.shape), v["zfactor"], v["half_w"], v["n_sub_blocks"], code, v.get("in_scale", 1.0))
+        descs.append(d)
+        n, H, W = s.shape
+        nout = (n - 1) * v["zfactor"] + 1
+        outs.append(torch.empty((nout, H, W), dtype=out_dtype(code), device=s.device))
+        vars_.append(torch.empty((nout, H, W), dtype=torch.float32, device=s.device) if want_var else None)
+        params.append(v["variogram"])
+    plan = Plan(descs, form=form, flags=flags, device=volumes[0]["slices"].device)
+    pt = variogram_tensor(params, device=volumes[0]["slices"].device)
+    plan.interpolate([v["slices"].contiguous() for v in volumes], outs, pt, vars_ if want_var else None, stream)
+    plan.device_status(stream)
+    plan.close()
+    return outs, vars_

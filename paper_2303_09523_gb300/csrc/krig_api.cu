@@ -1,0 +1,318 @@
+// krig_api.cu -- host side of the C ABI declared in include/krig.h: plan
+// creation (Algorithm 1 partition into Z sub-blocks and in-plane tiles,
+// geometry-class enumeration, workspace layout), argument checking, kernel
+// launches, device status and timing.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "krig_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+krig_status fail(krig_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+krig_status fail(krig_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+krig_status cuda_fail(int err, const char* what)
+{
+    return fail(KRIG_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Ordered distinct truncation slots along one axis of length N, half-width r.
+void axis_classes(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
+{
+    int n = 0;
+    for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) map[i] = -1;
+    std::vector<int> pos;
+    for (int p = 0; p < std::min(N, r + 1); ++p) pos.push_back(p);
+    for (int p = std::max(0, N - r - 1); p < N; ++p) pos.push_back(p);
+    for (int p : pos) {
+        int l = std::min(p, r), rr = std::min(N - 1 - p, r);
+        int slot = l * (r + 1) + rr;
+        if (map[slot] < 0) {
+            map[slot] = (int8_t)n;
+            ext[n][0] = (int8_t)l;
+            ext[n][1] = (int8_t)rr;
+            ++n;
+        }
+    }
+    *count = n;
+}
+
+struct Timing {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+}  // namespace
+
+struct krig_plan_s {
+    std::vector<krig_volume_desc> desc;
+    KrigLaunch L;
+    int form = KRIG_FORM_DS;
+    uint32_t flags = 0;
+    int64_t ws_bytes = 0;
+    unsigned char* ws = nullptr;
+    int timing = 0;
+    std::vector<Timing> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[KRIG_TIMING_KINDS] = {0, 0, 0, 0};
+    int64_t launches[KRIG_TIMING_KINDS] = {0, 0, 0, 0};
+};
+
+static krig_status check_desc(const krig_volume_desc& d, int i)
+{
+    if (d.H < 1 || d.H > 65536 || d.W < 1 || d.W > 65536)
+        return fail(KRIG_EINVAL, "volume %d: H, W must be in [1, 65536] (got %d x %d)", i, d.H, d.W);
+    if (d.n_known < 2 || d.n_known > 65536)
+        return fail(KRIG_EINVAL, "volume %d: n_known must be in [2, 65536] (got %d)", i, d.n_known);
+    if (d.zfactor < 1 || d.zfactor > KRIG_GMAX)
+        return fail(KRIG_EINVAL, "volume %d: zfactor must be in [1, %d] (got %d)", i, KRIG_GMAX, d.zfactor);
+    if (d.n_sub_blocks < 1 || d.n_sub_blocks > d.n_known - 1)
+        return fail(KRIG_EINVAL, "volume %d: n_sub_blocks must be in [1, n_known-1] (got %d)", i, d.n_sub_blocks);
+    if (d.half_w < 0 || d.half_w > KRIG_RMAX)
+        return fail(KRIG_EUNSUPPORTED, "volume %d: half_w must be in [0, %d] (got %d)", i, KRIG_RMAX, d.half_w);
+    if (d.in_dtype != KRIG_F64 && d.in_dtype != KRIG_F32 && d.in_dtype != KRIG_U16)
+        return fail(KRIG_EINVAL, "volume %d: unknown in_dtype %d", i, d.in_dtype);
+    if (d.in_dtype == KRIG_U16 && !(d.in_scale > 0.0f && d.in_scale < 3.0e38f))
+        return fail(KRIG_EINVAL, "volume %d: in_scale must be finite and > 0", i);
+    return KRIG_OK;
+}
+
+static krig_status record(krig_plan_t plan, cudaStream_t st, cudaEvent_t* ev)
+{
+    if (!plan->timing) return KRIG_OK;
+    if (plan->pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(KRIG_ECUDA, "cudaEventCreate failed");
+        plan->pool.push_back(e);
+    }
+    *ev = plan->pool.back();
+    plan->pool.pop_back();
+    if (cudaEventRecord(*ev, st) != cudaSuccess) return fail(KRIG_ECUDA, "cudaEventRecord failed");
+    return KRIG_OK;
+}
+
+template <typename F>
+static krig_status timed_launch(krig_plan_t plan, cudaStream_t st, int kind, F&& launch, const char* what)
+{
+    Timing t{nullptr, nullptr, kind};
+    krig_status s = record(plan, st, &t.a);
+    if (s != KRIG_OK) return s;
+    int err = launch();
+    if (err != 0) return cuda_fail(err, what);
+    s = record(plan, st, &t.b);
+    if (s != KRIG_OK) return s;
+    if (plan->timing) plan->pending.push_back(t);
+    return KRIG_OK;
+}
+
+extern "C" {
+
+int32_t krig_version(void) { return 100; }
+
+const char* krig_last_error(void) { return g_last_error.c_str(); }
+
+krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, int32_t n_vols, krig_form form,
+                             uint32_t flags, size_t* workspace_bytes_out)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (!vols) return fail(KRIG_EINVAL, "vols is NULL");
+    if (n_vols < 1 || n_vols > KRIG_MAX_VOLUMES)
+        return fail(KRIG_EINVAL, "n_vols must be in [1, %d] (got %d)", KRIG_MAX_VOLUMES, n_vols);
+    if (form != KRIG_FORM_P64 && form != KRIG_FORM_PMX && form != KRIG_FORM_DS)
+        return fail(KRIG_EINVAL, "unknown form %d", (int)form);
+    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE;
+    if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
+    for (int i = 0; i < n_vols; ++i) {
+        krig_status st = check_desc(vols[i], i);
+        if (st != KRIG_OK) return st;
+    }
+    krig_plan_s* p = new (std::nothrow) krig_plan_s();
+    if (!p) return fail(KRIG_ENOMEM, "out of host memory");
+    p->desc.assign(vols, vols + n_vols);
+    p->form = form;
+    p->flags = flags;
+    KrigLaunch& L = p->L;
+    memset(&L, 0, sizeof(L));
+    L.n_vols = n_vols;
+    L.form = form;
+    int64_t off = 256;  // control block: status word
+    int64_t items = 0, classes = 0, vox = 0;
+    for (int i = 0; i < n_vols; ++i) {
+        const krig_volume_desc& d = vols[i];
+        KrigVol& V = L.vol[i];
+        V.H = d.H;
+        V.W = d.W;
+        V.n = d.n_known;
+        V.g = d.zfactor;
+        V.k = d.n_sub_blocks;
+        V.r = d.half_w;
+        V.dtype = d.in_dtype;
+        V.scale = d.in_dtype == KRIG_U16 ? d.in_scale : 1.0f;
+        axis_classes(d.W, d.half_w, V.xmap, V.xext, &V.ncx);
+        axis_classes(d.H, d.half_w, V.ymap, V.yext, &V.ncy);
+        V.tiles_x = (d.W + KRIG_TX - 1) / KRIG_TX;
+        V.tiles_y = (d.H + KRIG_TY - 1) / KRIG_TY;
+        V.item_begin = items;
+        items += (int64_t)V.k * V.tiles_x * V.tiles_y;
+        V.cls_begin = classes;
+        if (V.g >= 2) classes += (int64_t)V.ncx * V.ncy;
+        V.vox_begin = vox;
+        vox += ((int64_t)(V.n - 1) * V.g + 1) * V.H * V.W;
+        if (form == KRIG_FORM_DS) {
+            V.wtab_off = off;
+            off = align_up(off + krig_wtab_bytes(V), 256);
+            V.vtab_off = off;
+            off = align_up(off + krig_vtab_bytes(V), 256);
+            V.lag_off = 0;
+        } else {
+            V.wtab_off = V.vtab_off = 0;
+            V.lag_off = off;
+            off = align_up(off + krig_lag_bytes(V), 256);
+        }
+    }
+    L.n_items = items;
+    L.n_classes = classes;
+    L.n_vox = vox;
+    p->ws_bytes = off;
+    if (workspace_bytes_out) *workspace_bytes_out = (size_t)off;
+    *plan = p;
+    return KRIG_OK;
+}
+
+krig_status krig_plan_set_workspace(krig_plan_t plan, void* d_workspace, size_t bytes)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (!d_workspace) return fail(KRIG_EWORKSPACE, "workspace is NULL");
+    if ((uintptr_t)d_workspace % 256 != 0) return fail(KRIG_EWORKSPACE, "workspace must be 256-byte aligned");
+    if ((int64_t)bytes < plan->ws_bytes)
+        return fail(KRIG_EWORKSPACE, "workspace too small: %zu bytes, plan needs %lld", bytes,
+                    (long long)plan->ws_bytes);
+    cudaError_t e = cudaMemset(d_workspace, 0, 256);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the workspace control block");
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the workspace control block");
+    plan->ws = (unsigned char*)d_workspace;
+    plan->L.ws = plan->ws;
+    plan->L.status = (uint32_t*)plan->ws;
+    return KRIG_OK;
+}
+
+krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void* const* d_out, float* const* d_var,
+                             const krig_variogram* d_params, void* stream)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (!plan->ws) return fail(KRIG_EWORKSPACE, "no workspace set (krig_plan_set_workspace)");
+    if (!d_slices || !d_out) return fail(KRIG_EINVAL, "d_slices / d_out is NULL");
+    if (!d_params) return fail(KRIG_EINVAL, "d_params is NULL");
+    KrigLaunch& L = plan->L;
+    for (int v = 0; v < L.n_vols; ++v) {
+        if (!d_slices[v] || !d_out[v]) return fail(KRIG_EINVAL, "volume %d: null slice or output pointer", v);
+        if ((uintptr_t)d_slices[v] % 16 || (uintptr_t)d_out[v] % 16)
+            return fail(KRIG_EINVAL, "volume %d: slice and output buffers must be 16-byte aligned", v);
+        if (d_var && d_var[v] && (uintptr_t)d_var[v] % 16)
+            return fail(KRIG_EINVAL, "volume %d: variance buffer must be 16-byte aligned", v);
+        L.in[v] = d_slices[v];
+        L.out[v] = d_out[v];
+        L.var[v] = d_var ? d_var[v] : nullptr;
+    }
+    L.vg = d_params;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->form == KRIG_FORM_DS) {
+        const int fp64 = (plan->flags & KRIG_FLAG_DS_FP64_SOLVE) ? 1 : 0;
+        krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_ds_solve(L, fp64, st); }, "class solve launch");
+        if (s != KRIG_OK) return s;
+        s = timed_launch(plan, st, 1, [&] { return krig_launch_ds_apply(L, 0, st); }, "stencil launch");
+        if (s != KRIG_OK) return s;
+    } else {
+        krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_voxel(L, plan->form, st); }, "voxel solve launch");
+        if (s != KRIG_OK) return s;
+    }
+    return KRIG_OK;
+}
+
+krig_status krig_plan_device_status(krig_plan_t plan, void* stream)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (!plan->ws) return fail(KRIG_EWORKSPACE, "no workspace set");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    uint32_t bits = 0;
+    e = cudaMemcpy(&bits, plan->ws, sizeof(bits), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+    if (bits) {
+        e = cudaMemset(plan->ws, 0, sizeof(bits));
+        if (e != cudaSuccess) return cuda_fail(e, "clearing the device status");
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "clearing the device status");
+    }
+    if (bits & KRIG_DEV_SINGULAR) return fail(KRIG_ESINGULAR, "a kriging system was singular (check nugget + sill > 0)");
+    if (bits & KRIG_DEV_TIMEOUT) return fail(KRIG_ETIMEOUT, "a device-side wait timed out");
+    return KRIG_OK;
+}
+
+krig_status krig_plan_set_timing(krig_plan_t plan, int32_t enable)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    plan->timing = enable ? 1 : 0;
+    return KRIG_OK;
+}
+
+krig_status krig_plan_get_timing(krig_plan_t plan, double* ms_out, int64_t* launches_out)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    for (Timing& t : plan->pending) {
+        cudaError_t e = cudaEventSynchronize(t.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e != cudaSuccess) return cuda_fail(e, "reading timing events");
+        plan->ms[t.kind] += ms;
+        plan->launches[t.kind] += 1;
+        plan->pool.push_back(t.a);
+        plan->pool.push_back(t.b);
+    }
+    plan->pending.clear();
+    for (int k = 0; k < KRIG_TIMING_KINDS; ++k) {
+        if (ms_out) ms_out[k] = plan->ms[k];
+        if (launches_out) launches_out[k] = plan->launches[k];
+        plan->ms[k] = 0;
+        plan->launches[k] = 0;
+    }
+    return KRIG_OK;
+}
+
+void krig_plan_destroy(krig_plan_t plan)
+{
+    if (!plan) return;
+    for (Timing& t : plan->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : plan->pool) cudaEventDestroy(e);
+    delete plan;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// krig_voxel.cu -- the per-voxel forms of the kriging path.
+//
+// Every missing voxel gathers its own neighbourhood (the (2r+1)^2 window in
+// each bracketing known slice, truncated at the in-plane border), builds its
+// own extended ordinary-kriging system (Appendix A with one constant
+// predictor), solves it and forms the weighted sum and the kriging variance
+// (Sec. 4.1.2).  One warp per voxel.
+//   P64: FP64 Cholesky factorisation and solves.
+//   PMX: FP32 factorisation and solves plus one FP64 iterative-refinement step.
+// The covariances at the few distinct lags of a volume are tabulated once per
+// call in FP64 (k_lag) and looked up while each voxel builds its matrix.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "krig_device.cuh"
+
+__global__ void __launch_bounds__(256) k_lag(const __grid_constant__ KrigLaunch P)
+{
+    const int v = blockIdx.x;
+    const KrigVol& V = P.vol[v];
+    if (V.g < 2) return;
+    LagDims d{V.r, V.g, 2 * V.r + 1, V.r + 1};
+    double* gC = (double*)(P.ws + V.lag_off);
+    double* g0 = gC + d.nC();
+    const krig_variogram vg = P.vg[v];
+    krig_fill_lags(d, vg, gC, g0, threadIdx.x, 256);
+}
+
+__device__ __forceinline__ double in_value(const void* in, int dtype, float scale, int64_t idx)
+{
+    if (dtype == KRIG_F64) return ((const double*)in)[idx];
+    if (dtype == KRIG_F32) return (double)((const float*)in)[idx];
+    return (double)__fmul_rn((float)((const uint16_t*)in)[idx], scale);
+}
+
+template <typename TF, int KM>
+__global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunch P)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typedef SolveSmem<TF, KM, 2> Smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Smem& S = ((Smem*)smraw)[warp];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t vox = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; vox < P.n_vox; vox += nwarps) {
+        const int v = krig_find_vol(P, vox, 2);
+        const KrigVol& V = P.vol[v];
+        const int64_t local = vox - V.vox_begin;
+        const int64_t plane = (int64_t)V.H * V.W;
+        const int z = (int)(local / plane);
+        const int64_t pix = local % plane;
+        const int y = (int)(pix / V.W), x = (int)(pix % V.W);
+        const int g = V.g, j = z / g, t = z % g;
+        const bool f64 = V.dtype == KRIG_F64;
+        if (t == 0) {  // known slice: copy through
+            if (lane == 0) {
+                double val = in_value(P.in[v], V.dtype, V.scale, (int64_t)j * plane + pix);
+                if (f64) ((double*)P.out[v])[local] = val;
+                else ((float*)P.out[v])[local] = (float)val;
+                if (P.var[v]) P.var[v][local] = 0.0f;
+            }
+            continue;
+        }
+        const int r = V.r;
+        LagDims d{r, g, 2 * r + 1, r + 1};
+        const double* gC = (const double*)(P.ws + V.lag_off);
+        const double* g0 = gC + d.nC();
+        const int lx = min(x, r), rx = min(V.W - 1 - x, r), ly = min(y, r), ry = min(V.H - 1 - y, r);
+        const int nx = lx + rx + 1, ny = ly + ry + 1;
+        const int K = 2 * nx * ny;
+        __syncwarp();
+        for (int i = lane; i < K; i += 32) {
+            Tap tp;
+            tp.s = (int8_t)(i / (nx * ny));
+            tp.dy = (int8_t)((i / nx) % ny - ly);
+            tp.dx = (int8_t)(i % nx - lx);
+            tp.pad = 0;
+            S.tap[i] = tp;
+            S.Bd[i * 2 + 0] = __ldg(g0 + d.i0(t, tp.s, abs((int)tp.dy), abs((int)tp.dx)));
+            S.Bd[i * 2 + 1] = 1.0;
+        }
+        __syncwarp();
+        const bool ok = team_ok_solve<TF, KM, 2, 32>(S, d, gC, K, 2, lane);
+        double est = 0.0, var = 0.0;
+        if (ok) {
+            double su = 0.0, sv = 0.0;
+            for (int i = lane; i < K; i += 32) {
+                su += S.Xd[i * 2 + 0];
+                sv += S.Xd[i * 2 + 1];
+            }
+            for (int o = 16; o; o >>= 1) {
+                su += __shfl_xor_sync(0xffffffffu, su, o);
+                sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            }
+            const double phi = (su - 1.0) / sv;
+            double wz = 0.0, wc = 0.0;
+            for (int i = lane; i < K; i += 32) {
+                Tap tp = S.tap[i];
+                double w = S.Xd[i * 2 + 0] - phi * S.Xd[i * 2 + 1];
+                int64_t idx = (int64_t)(j + tp.s) * plane + (int64_t)(y + tp.dy) * V.W + (x + tp.dx);
+                wz += w * in_value(P.in[v], V.dtype, V.scale, idx);
+                wc += w * S.Bd[i * 2 + 0];
+            }
+            for (int o = 16; o; o >>= 1) {
+                wz += __shfl_xor_sync(0xffffffffu, wz, o);
+                wc += __shfl_xor_sync(0xffffffffu, wc, o);
+            }
+            est = wz;
+            var = gC[0] - wc - phi;
+        } else {
+            est = var = __longlong_as_double(0x7ff8000000000000LL);
+            if (lane == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
+        }
+        if (lane == 0) {
+            if (f64) ((double*)P.out[v])[local] = est;
+            else ((float*)P.out[v])[local] = (float)est;
+            if (P.var[v]) P.var[v][local] = (float)var;
+        }
+    }
+}
+
+template <typename TF, int KM>
+static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st)
+{
+    const size_t smem = 8 * sizeof(SolveSmem<TF, KM, 2>);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_voxel<TF, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxel<TF, KM>, 256, smem);
+    if (e != cudaSuccess) return (int)e;
+    int sms = krig_device_sm_count();
+    int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    int64_t need = (L.n_vox + 7) / 8;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_voxel<TF, KM><<<(unsigned)grid, 256, smem, st>>>(L);
+    return (int)cudaGetLastError();
+}
+
+int krig_launch_voxel(const KrigLaunch& L, int form, void* stream)
+{
+    if (L.n_vox == 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_lag<<<L.n_vols, 256, 0, st>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    int rmax = 0;
+    for (int v = 0; v < L.n_vols; ++v) rmax = L.vol[v].r > rmax ? L.vol[v].r : rmax;
+    const bool fp64 = form == KRIG_FORM_P64;
+    if (rmax == 0) return fp64 ? launch_voxel_t<double, 2>(L, st) : launch_voxel_t<float, 2>(L, st);
+    if (rmax == 1) return fp64 ? launch_voxel_t<double, 18>(L, st) : launch_voxel_t<float, 18>(L, st);
+    return fp64 ? launch_voxel_t<double, 50>(L, st) : launch_voxel_t<float, 50>(L, st);
+}
