@@ -158,6 +158,36 @@ const char* krig_last_error(void);
  * NULL is ignored. */
 void krig_plan_destroy(krig_plan_t plan);
 
+/* Interpolate ONE volume in the DS form without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory -- a plugin inside an application that owns all
+ * device memory through its own pool, a real-time loop that cannot take
+ * cudaMalloc's implicit device synchronisation, a service under a device
+ * memory budget enforced outside this library.  They cannot supply the
+ * workspace krig_plan_set_workspace needs.
+ *
+ * Scratch: a static device array of 64 KiB inside the library, held by every
+ * GPU that loads the library until the process exits.  Volumes whose class
+ * tables do not fit are rejected with KRIG_EINVAL and a message giving the
+ * size needed (float64 input with half_w 2 needs about 81 KB; every float32 or
+ * uint16 volume fits).  Every call shares that one array and leaves its last
+ * contents in it; the call clears the device status word itself.  Calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on the
+ * scratch and must be serialised by the caller.
+ *
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device, done with that device current); make that first call
+ * before any stream capture.
+ *
+ * Arguments: as one volume of krig_interpolate (desc, d_slices, d_out,
+ * d_var nullable, d_params pointing at one device krig_variogram).  With
+ * check_status != 0 the call waits for the stream and returns KRIG_ESINGULAR
+ * if a kriging system was singular; with 0 it returns after enqueueing (a
+ * singular system then shows as NaN estimates).  No cudaMalloc, cudaFree or
+ * other allocating call is made. */
+krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out, float* d_var,
+                                     const krig_variogram* d_params, int32_t check_status, void* stream);
+
 /* Library version: major * 10000 + minor * 100 + patch. */
 int32_t krig_version(void);
 

@@ -59,6 +59,12 @@ void axis_classes(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
     *count = n;
 }
 
+}  // namespace
+
+void krig_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+
 struct Timing {
     cudaEvent_t a, b;
     int kind;

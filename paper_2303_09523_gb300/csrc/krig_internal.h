@@ -63,6 +63,9 @@ int krig_launch_ds_apply(const KrigLaunch& L, int grid, void* stream);
 int krig_launch_voxel(const KrigLaunch& L, int form, void* stream);
 int krig_device_sm_count();
 
+// Set the thread-local message returned by krig_last_error() (krig_api.cu).
+__attribute__((visibility("hidden"))) void krig_internal_set_error(const char* msg);
+
 // Table sizes (bytes) per volume for the DS form.
 inline int64_t krig_wtab_bytes(const KrigVol& v)
 {

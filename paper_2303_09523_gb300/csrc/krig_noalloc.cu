@@ -1,0 +1,158 @@
+// krig_noalloc.cu -- krig_interpolate_noalloc: the DS interpolation of one
+// volume without any device allocation by the caller or by the library.
+//
+// Who needs it: code that may not call cudaMalloc at all -- plugins hosted by
+// an application that owns every device byte through its own memory pool,
+// real-time pipelines that cannot afford cudaMalloc's implicit device-wide
+// synchronisation in their frame loop, or services that run under a fixed
+// device-memory budget enforced outside the library.  Such callers cannot
+// provide the workspace that krig_plan_set_workspace expects.
+//
+// Instead the scratch (device status word, per-class weight and variance
+// tables) lives in one file-scope __device__ array of KRIG_NOALLOC_SCRATCH_BYTES
+// that every GPU loading the library keeps until the process exits.  Host code
+// cannot pass that array's name to a kernel (on the host it only names a
+// host-side stand-in), so the device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "krig_internal.h"
+
+#define KRIG_NOALLOC_SCRATCH_BYTES (64 * 1024)
+#define KRIG_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_krig_noalloc_scratch[KRIG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[KRIG_NOALLOC_MAX_DEVICES];
+
+krig_status noalloc_fail(krig_status st, const std::string& msg)
+{
+    krig_internal_set_error(msg.c_str());  // reported by krig_last_error()
+    return st;
+}
+
+// Device address of the static scratch on the current device (set-up on the
+// first call per device).
+krig_status noalloc_scratch(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(KRIG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= KRIG_NOALLOC_MAX_DEVICES) return noalloc_fail(KRIG_EUNSUPPORTED, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_krig_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(KRIG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return KRIG_OK;
+}
+
+// Truncation classes along one axis (no heap use).
+void noalloc_axis(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
+{
+    int n = 0;
+    for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) map[i] = -1;
+    for (int p = 0; p < N; ++p) {
+        if (p > r && p < N - r - 1) continue;  // interior positions repeat the class at p = r
+        int l = p < r ? p : r, rr = (N - 1 - p) < r ? (N - 1 - p) : r;
+        int slot = l * (r + 1) + rr;
+        if (map[slot] < 0) {
+            map[slot] = (int8_t)n;
+            ext[n][0] = (int8_t)l;
+            ext[n][1] = (int8_t)rr;
+            ++n;
+        }
+    }
+    *count = n;
+}
+
+}  // namespace
+
+extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out,
+                                                float* d_var, const krig_variogram* d_params, int32_t check_status,
+                                                void* stream)
+{
+    if (!desc || !d_slices || !d_out || !d_params)
+        return noalloc_fail(KRIG_EINVAL, "desc, d_slices, d_out and d_params must not be NULL");
+    const krig_volume_desc& d = *desc;
+    if (d.H < 1 || d.H > 65536 || d.W < 1 || d.W > 65536 || d.n_known < 2 || d.n_known > 65536 ||
+        d.zfactor < 1 || d.zfactor > KRIG_GMAX || d.n_sub_blocks < 1 || d.n_sub_blocks > d.n_known - 1 ||
+        d.half_w < 0 || d.half_w > KRIG_RMAX ||
+        (d.in_dtype != KRIG_F64 && d.in_dtype != KRIG_F32 && d.in_dtype != KRIG_U16) ||
+        (d.in_dtype == KRIG_U16 && !(d.in_scale > 0.0f && d.in_scale < 3.0e38f)))
+        return noalloc_fail(KRIG_EINVAL, "invalid volume descriptor (same limits as krig_plan_create)");
+    if ((uintptr_t)d_slices % 16 || (uintptr_t)d_out % 16 || (d_var && (uintptr_t)d_var % 16))
+        return noalloc_fail(KRIG_EINVAL, "slice, output and variance buffers must be 16-byte aligned");
+
+    // The kernel parameter block is built on the stack.
+    static_assert(sizeof(KrigLaunch) < 64 * 1024, "launch block too large for the stack");
+    KrigLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.n_vols = 1;
+    L.form = KRIG_FORM_DS;
+    KrigVol& V = L.vol[0];
+    V.H = d.H;
+    V.W = d.W;
+    V.n = d.n_known;
+    V.g = d.zfactor;
+    V.k = d.n_sub_blocks;
+    V.r = d.half_w;
+    V.dtype = d.in_dtype;
+    V.scale = d.in_dtype == KRIG_U16 ? d.in_scale : 1.0f;
+    noalloc_axis(d.W, d.half_w, V.xmap, V.xext, &V.ncx);
+    noalloc_axis(d.H, d.half_w, V.ymap, V.yext, &V.ncy);
+    V.tiles_x = (d.W + KRIG_TX - 1) / KRIG_TX;
+    V.tiles_y = (d.H + KRIG_TY - 1) / KRIG_TY;
+    V.item_begin = 0;
+    V.cls_begin = 0;
+    V.vox_begin = 0;
+    V.wtab_off = 256;
+    V.vtab_off = (V.wtab_off + krig_wtab_bytes(V) + 255) / 256 * 256;
+    const int64_t need = (V.vtab_off + krig_vtab_bytes(V) + 255) / 256 * 256;
+    if (need > KRIG_NOALLOC_SCRATCH_BYTES)
+        return noalloc_fail(KRIG_EINVAL, "this volume needs " + std::to_string((long long)need) +
+                                             " bytes of scratch; the static scratch holds " +
+                                             std::to_string(KRIG_NOALLOC_SCRATCH_BYTES) +
+                                             " (use krig_plan_create with a caller workspace instead)");
+    L.n_items = (int64_t)V.k * V.tiles_x * V.tiles_y;
+    L.n_classes = V.g >= 2 ? (int64_t)V.ncx * V.ncy : 0;
+    L.n_vox = ((int64_t)(V.n - 1) * V.g + 1) * V.H * V.W;
+
+    void* scratch = nullptr;
+    krig_status st = noalloc_scratch(&scratch);
+    if (st != KRIG_OK) return st;
+    L.ws = (unsigned char*)scratch;
+    L.status = (uint32_t*)scratch;
+    L.in[0] = d_slices;
+    L.out[0] = d_out;
+    L.var[0] = d_var;
+    L.vg = d_params;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 256, s);  // the status word must start at zero
+    if (e != cudaSuccess) return noalloc_fail(KRIG_ECUDA, std::string("clearing the status word: ") + cudaGetErrorString(e));
+    int err = krig_launch_ds_solve(L, 0, s);
+    if (err) return noalloc_fail(KRIG_ECUDA, std::string("class solve launch: ") + cudaGetErrorString((cudaError_t)err));
+    err = krig_launch_ds_apply(L, 0, s);
+    if (err) return noalloc_fail(KRIG_ECUDA, std::string("stencil launch: ") + cudaGetErrorString((cudaError_t)err));
+    if (check_status) {
+        uint32_t bits = 0;
+        e = cudaMemcpyAsync(&bits, scratch, sizeof(bits), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return noalloc_fail(KRIG_ECUDA, std::string("reading the status word: ") + cudaGetErrorString(e));
+        if (bits & KRIG_DEV_SINGULAR) return noalloc_fail(KRIG_ESINGULAR, "a kriging system was singular");
+    }
+    return KRIG_OK;
+}
