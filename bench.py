@@ -289,7 +289,9 @@ def main():
 
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = compare_forms(args, vol, s_dev, desc, params, out, dev, stream)
+        peaks = {"fp32_fma_gflops": binding.measure_fma_peak(False), "fp64_fma_gflops": binding.measure_fma_peak(True)}
+        extra = compare_forms(args, vol, s_dev, desc, params, out, dev, stream, peaks)
+        extra["alu_peaks_measured"] = peaks
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -323,7 +325,13 @@ def main():
         dist.destroy_process_group()
 
 
-def compare_forms(args, vol, s_dev, desc, params, out_ds, dev, stream):
+def p64_flops_per_voxel(vol):
+    """FP64 flops of one interior voxel's P64 solve: Cholesky K^3/3, four triangular sweeps 4K^2, combine 6K."""
+    K = 2 * (2 * vol.half_w + 1) ** 2
+    return K ** 3 / 3.0 + 4.0 * K * K + 6.0 * K
+
+
+def compare_forms(args, vol, s_dev, desc, params, out_ds, dev, stream, peaks):
     """Plain FP64 per-voxel form (P64) and the mixed per-voxel form (PMX) on the same workload."""
     import torch
     from paper_2303_09523_gb300 import binding
@@ -345,6 +353,11 @@ def compare_forms(args, vol, s_dev, desc, params, out_ds, dev, stream):
         res[form] = {"value": vol.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms}
         if form == "P64":
             ref = o.double()
+            gfl = p64_flops_per_voxel(vol) * vol.n_missing / (ms * 1e-3) / 1e9
+            res[form]["fp64_roofline"] = {"bound": "fp64", "achieved": gfl, "peak": peaks["fp64_fma_gflops"],
+                                          "unit": "GFLOP/s", "frac": gfl / peaks["fp64_fma_gflops"],
+                                          "flops_per_voxel": p64_flops_per_voxel(vol),
+                                          "peak_source": "krig_measure_fma_peak (FP64 FMA microbenchmark)"}
         else:
             res[form]["max_rel_err_vs_P64"] = float((o.double() - ref).abs().max() / ref.abs().max())
         plan.close()

@@ -105,6 +105,11 @@ typedef struct {
  *   KRIG_FLAG_DS_FP64_SOLVE: DS form only -- factorise the class systems in
  *   FP64 instead of FP32 followed by one FP64 iterative-refinement step. */
 #define KRIG_FLAG_DS_FP64_SOLVE 0x1u
+/*   KRIG_FLAG_FAULT_TIMEOUT: test only -- the DS stencil kernel waits once on a
+ *   barrier that nothing completes, so its bounded wait gives up and the call's
+ *   device status becomes KRIG_ETIMEOUT (exercises failure detection without a
+ *   real fault; the outputs of that call are not valid). */
+#define KRIG_FLAG_FAULT_TIMEOUT 0x100u
 
 #define KRIG_MAX_VOLUMES 64
 
@@ -187,6 +192,13 @@ void krig_plan_destroy(krig_plan_t plan);
  * other allocating call is made. */
 krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out, float* d_var,
                                      const krig_variogram* d_params, int32_t check_status, void* stream);
+
+/* Measure the device's fused multiply-add rate (GFLOP/s, 2 flops per FMA)
+ * in FP32 (fp64 = 0) or FP64 (fp64 = 1) on the current device with a short
+ * synchronous kernel.  Support routine: the roofline denominator for kernels
+ * bound by arithmetic issue rather than memory.  Errors: KRIG_EINVAL,
+ * KRIG_ECUDA. */
+krig_status krig_measure_fma_peak(int32_t fp64, double* gflops_out);
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 int32_t krig_version(void);

@@ -77,6 +77,8 @@ def lib(build_if_missing: bool = False):
     L.krig_last_error.restype = ctypes.c_char_p
     L.krig_plan_destroy.argtypes = [vp]
     L.krig_plan_destroy.restype = None
+    L.krig_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.krig_measure_fma_peak.restype = ctypes.c_int
     L.krig_version.argtypes = []
     L.krig_version.restype = ctypes.c_int32
     _lib = L
@@ -178,6 +180,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def measure_fma_peak(fp64: bool) -> float:
+    """FP32 or FP64 fused multiply-add peak of the current device, GFLOP/s."""
+    g = ctypes.c_double()
+    _check(lib().krig_measure_fma_peak(1 if fp64 else 0, ctypes.byref(g)))
+    return g.value
 
 
 def desc_for(slices_shape, zfactor, half_w, n_sub_blocks, dtype_code_, in_scale=1.0):

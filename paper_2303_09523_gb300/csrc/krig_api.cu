@@ -38,27 +38,6 @@ krig_status cuda_fail(int err, const char* what)
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Ordered distinct truncation slots along one axis of length N, half-width r.
-void axis_classes(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
-{
-    int n = 0;
-    for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) map[i] = -1;
-    std::vector<int> pos;
-    for (int p = 0; p < std::min(N, r + 1); ++p) pos.push_back(p);
-    for (int p = std::max(0, N - r - 1); p < N; ++p) pos.push_back(p);
-    for (int p : pos) {
-        int l = std::min(p, r), rr = std::min(N - 1 - p, r);
-        int slot = l * (r + 1) + rr;
-        if (map[slot] < 0) {
-            map[slot] = (int8_t)n;
-            ext[n][0] = (int8_t)l;
-            ext[n][1] = (int8_t)rr;
-            ++n;
-        }
-    }
-    *count = n;
-}
-
 }  // namespace
 
 void krig_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
@@ -149,7 +128,7 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         return fail(KRIG_EINVAL, "n_vols must be in [1, %d] (got %d)", KRIG_MAX_VOLUMES, n_vols);
     if (form != KRIG_FORM_P64 && form != KRIG_FORM_PMX && form != KRIG_FORM_DS)
         return fail(KRIG_EINVAL, "unknown form %d", (int)form);
-    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE;
+    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT;
     if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
     for (int i = 0; i < n_vols; ++i) {
         krig_status st = check_desc(vols[i], i);
@@ -164,41 +143,13 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
     memset(&L, 0, sizeof(L));
     L.n_vols = n_vols;
     L.form = form;
+    L.fault_timeout = (flags & KRIG_FLAG_FAULT_TIMEOUT) ? 1 : 0;
     int64_t off = 256;  // control block: status word
-    int64_t items = 0, classes = 0, vox = 0;
-    for (int i = 0; i < n_vols; ++i) {
-        const krig_volume_desc& d = vols[i];
-        KrigVol& V = L.vol[i];
-        V.H = d.H;
-        V.W = d.W;
-        V.n = d.n_known;
-        V.g = d.zfactor;
-        V.k = d.n_sub_blocks;
-        V.r = d.half_w;
-        V.dtype = d.in_dtype;
-        V.scale = d.in_dtype == KRIG_U16 ? d.in_scale : 1.0f;
-        axis_classes(d.W, d.half_w, V.xmap, V.xext, &V.ncx);
-        axis_classes(d.H, d.half_w, V.ymap, V.yext, &V.ncy);
-        V.tiles_x = (d.W + KRIG_TX - 1) / KRIG_TX;
-        V.tiles_y = (d.H + KRIG_TY - 1) / KRIG_TY;
-        V.item_begin = items;
-        items += (int64_t)V.k * V.tiles_x * V.tiles_y;
-        V.cls_begin = classes;
-        if (V.g >= 2) classes += (int64_t)V.ncx * V.ncy;
-        V.vox_begin = vox;
-        vox += ((int64_t)(V.n - 1) * V.g + 1) * V.H * V.W;
-        if (form == KRIG_FORM_DS) {
-            V.wtab_off = off;
-            off = align_up(off + krig_wtab_bytes(V), 256);
-            V.vtab_off = off;
-            off = align_up(off + krig_vtab_bytes(V), 256);
-            V.lag_off = 0;
-        } else {
-            V.wtab_off = V.vtab_off = 0;
-            V.lag_off = off;
-            off = align_up(off + krig_lag_bytes(V), 256);
-        }
-    }
+    int64_t items = 0, classes = 0, vox = 0, frames = 0;
+    const int chunk = krig_pick_chunk(vols, n_vols);
+    for (int i = 0; i < n_vols; ++i)
+        krig_fill_vol(L.vol[i], vols[i], form, chunk, &off, &items, &classes, &vox, &frames);
+    L.n_frame_units = frames;
     L.n_items = items;
     L.n_classes = classes;
     L.n_vox = vox;

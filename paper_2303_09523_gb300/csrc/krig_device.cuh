@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "krig_internal.h"
 
 // Covariance C(h) = C(0) - gamma(h) at squared lag h2, written so that no
@@ -229,4 +231,375 @@ __device__ __forceinline__ int krig_find_vol(const KrigLaunch& P, int64_t idx, i
         if (b <= idx) v = u;
     }
     return v;
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident FP32 factorisation for one warp.
+//
+// Lane l holds rows i = l + 32q (q < ROWS) of the KM x KM matrix in a[q][*];
+// rows and columns past the system size K are identity, so the leading K x K
+// block factors exactly as if alone.  Right-looking Cholesky: at step k the
+// pivot and column k are broadcast with warp shuffles, and each lane updates
+// its own rows.  All loop bounds are compile-time, so the matrix never leaves
+// registers.  Returns false (warp-uniform) if a pivot is not positive.
+// ---------------------------------------------------------------------------
+template <int KM>
+struct RegDim {
+    static constexpr int ROWS = (KM + 31) / 32;
+    static constexpr int LDL = KM + 1;  // odd leading dimension of L in shared memory
+};
+
+// Compile-time loop: calls f(integral_constant<int, i>) for i in [B, E).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+template <int KM, typename T = float>
+__device__ __forceinline__ bool warp_chol_reg(T (&a)[RegDim<KM>::ROWS][KM], int lane)
+{
+    constexpr int ROWS = RegDim<KM>::ROWS;
+    bool ok = true;
+    static_for<0, KM>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const T piv = __shfl_sync(0xffffffffu, a[k / 32][k], k % 32);
+        ok = ok && (piv > T(0));
+        const T l = sqrt(piv);
+        const T il = T(1) / l;
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i > k) a[q][k] *= il;
+            else if (i == k) a[q][k] = l;
+        }
+        static_for<k + 1, KM>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const T ljk = __shfl_sync(0xffffffffu, a[j / 32][k], j % 32);
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) {
+                const int i = lane + 32 * q;
+                if (i >= j) a[q][j] = fma(-a[q][k], ljk, a[q][j]);
+            }
+        });
+    });
+    return ok;
+}
+
+// Store the factor (lower triangle, row-major, leading dimension KM+1) and the
+// reciprocal diagonal to shared memory.
+template <int KM, typename T = float>
+__device__ __forceinline__ void warp_store_factor(const T (&a)[RegDim<KM>::ROWS][KM], T* Ls, T* dinv, int lane)
+{
+    constexpr int ROWS = RegDim<KM>::ROWS, LDL = RegDim<KM>::LDL;
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int i = lane + 32 * q;
+        if (i < KM) {
+#pragma unroll
+            for (int j = 0; j < KM; ++j)
+                if (j <= i) Ls[i * LDL + j] = a[q][j];
+#pragma unroll
+            for (int j = 0; j < KM; ++j)
+                if (j == i) dinv[i] = T(1) / a[q][j];
+        }
+    }
+}
+
+// Solve L L' x = x for one right-hand side held by the warp (lane l owns
+// x[q] = x_{l+32q}), with L and 1/diag(L) in shared memory.
+template <int KM, typename T = float>
+__device__ __forceinline__ void warp_sweep(const T* Ls, const T* dinv, T (&x)[RegDim<KM>::ROWS], int lane)
+{
+    constexpr int ROWS = RegDim<KM>::ROWS, LDL = RegDim<KM>::LDL;
+    static_for<0, KM>([&](auto kc) {  // forward: L y = b
+        constexpr int k = decltype(kc)::value;
+        const T xk = __shfl_sync(0xffffffffu, x[k / 32], k % 32) * dinv[k];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i == k) x[q] = xk;
+            else if (i > k && i < KM) x[q] = fma(-Ls[i * LDL + k], xk, x[q]);
+        }
+    });
+    static_for<0, KM>([&](auto kc) {  // backward: L' x = y
+        constexpr int k = KM - 1 - decltype(kc)::value;
+        const T xk = __shfl_sync(0xffffffffu, x[k / 32], k % 32) * dinv[k];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i == k) x[q] = xk;
+            else if (i < k) x[q] = fma(-Ls[k * LDL + i], xk, x[q]);
+        }
+    });
+}
+
+// Shared memory of one block-wide class solve with the register factorisation.
+template <int KM>
+struct RegSolveSmem {
+    float Ls[KM * (KM + 1)];
+    float dinv[KM];
+    float Xf[KM * 8];      // float staging of right-hand sides / residuals
+    double Bd[KM * 8];     // FP64 right-hand sides
+    double Xd[KM * 8];     // FP64 solutions
+    Tap tap[KM];
+    int flag;
+};
+
+// Block-wide (NT threads, NT/32 >= NC warps) ordinary-kriging solve of one
+// geometry class with the register factorisation: warp 0 factors C in FP32,
+// warp c sweeps right-hand side c, all threads form the FP64 residual
+// B - C X, the warps sweep the correction, and S.Xd receives the refined
+// FP64 solution.  Taps beyond K are identity-padded.  C comes from the FP64
+// lag table gC.  Returns false if C was not positive definite.
+template <int KM, int NT>
+__device__ bool block_ok_solve_reg(RegSolveSmem<KM>& S, const LagDims& d, const double* gC, int K, int NC, int tid)
+{
+    constexpr int ROWS = RegDim<KM>::ROWS;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        float a[ROWS][KM];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            const Tap ti = S.tap[i < K ? i : 0];
+#pragma unroll
+            for (int j = 0; j < KM; ++j) {
+                float v;
+                if (i < K && j < K) v = (float)krig_cij(d, gC, ti, S.tap[j]);
+                else v = (i == j) ? 1.0f : 0.0f;
+                a[q][j] = v;
+            }
+        }
+        const bool ok = warp_chol_reg<KM>(a, lane);
+        if (ok) warp_store_factor<KM>(a, S.Ls, S.dinv, lane);
+        if (lane == 0) S.flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!S.flag) return false;
+    // first solve, one warp per right-hand side
+    if (warp < NC) {
+        float x[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = i < K ? (float)S.Bd[i * 8 + warp] : 0.0f;
+        }
+        warp_sweep<KM>(S.Ls, S.dinv, x, lane);
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i < K) S.Xd[i * 8 + warp] = (double)x[q];
+        }
+    }
+    __syncthreads();
+    // FP64 residual of every column
+    for (int e = tid; e < K * NC; e += NT) {
+        const int i = e / NC, c = e % NC;
+        double s = S.Bd[i * 8 + c];
+        const Tap ti = S.tap[i];
+        for (int j = 0; j < K; ++j) s -= krig_cij(d, gC, ti, S.tap[j]) * S.Xd[j * 8 + c];
+        S.Xf[i * 8 + c] = (float)s;
+    }
+    __syncthreads();
+    // correction solve and update
+    if (warp < NC) {
+        float x[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = i < K ? S.Xf[i * 8 + warp] : 0.0f;
+        }
+        warp_sweep<KM>(S.Ls, S.dinv, x, lane);
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i < K) S.Xd[i * 8 + warp] += (double)x[q];
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Per-warp shared memory of a per-voxel solve (two right-hand sides: c0 and ones).
+template <int KM, typename T>
+struct VoxSmem {
+    T Ls[KM * (KM + 1)];
+    T dinv[KM];
+    double Bd[KM * 2];
+    double Xd[KM * 2];
+    Tap tap[KM];
+};
+
+// One warp solves one voxel's system with the register factorisation.
+// T = double: FP64 factorisation and sweeps (no refinement).  T = float:
+// FP32 factorisation and sweeps plus one FP64 refinement step (the residual
+// B - C X is formed in FP64 from the FP64 lag table).  On return S.Xd holds
+// u (column 0) and v (column 1) in FP64.
+template <int KM, typename T>
+__device__ bool warp_ok_solve_vox(VoxSmem<KM, T>& S, const LagDims& d, const double* gC, int K, int lane)
+{
+    constexpr int ROWS = RegDim<KM>::ROWS;
+    T a[ROWS][KM];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int i = lane + 32 * q;
+        const Tap ti = S.tap[i < K ? i : 0];
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {
+            T v;
+            if (i < K && j < K) v = (T)krig_cij(d, gC, ti, S.tap[j]);
+            else v = (i == j) ? T(1) : T(0);
+            a[q][j] = v;
+        }
+    }
+    const bool ok = warp_chol_reg<KM, T>(a, lane);
+    if (!ok) return false;
+    warp_store_factor<KM, T>(a, S.Ls, S.dinv, lane);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        T x[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = i < K ? (T)S.Bd[i * 2 + c] : T(0);
+        }
+        warp_sweep<KM, T>(S.Ls, S.dinv, x, lane);
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            if (i < K) S.Xd[i * 2 + c] = (double)x[q];
+        }
+    }
+    __syncwarp();
+    if (sizeof(T) == 4) {
+        T rres[2][ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = lane + 32 * q;
+            double s0 = 0.0, s1 = 0.0;
+            if (i < K) {
+                s0 = S.Bd[i * 2 + 0];
+                s1 = S.Bd[i * 2 + 1];
+                const Tap ti = S.tap[i];
+                for (int j = 0; j < K; ++j) {
+                    const double cij = krig_cij(d, gC, ti, S.tap[j]);
+                    s0 -= cij * S.Xd[j * 2 + 0];
+                    s1 -= cij * S.Xd[j * 2 + 1];
+                }
+            }
+            rres[0][q] = (T)s0;
+            rres[1][q] = (T)s1;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            warp_sweep<KM, T>(S.Ls, S.dinv, rres[c], lane);
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) {
+                const int i = lane + 32 * q;
+                if (i < K) S.Xd[i * 2 + c] += (double)rres[c][q];
+            }
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Block-parallel inversion for the class solves.
+//
+// Gauss-Jordan elimination of [C | I] in FP32 shared memory by the whole
+// block, without row scaling: at step k every row i != k subtracts
+// (a_ik / a_kk) times row k over the columns that can still be nonzero
+// (k+1..K-1 of the left half, 0..k of the right half), so one barrier per
+// step suffices.  C is SPD, so diagonal pivots are positive and no pivoting
+// is needed.  Afterwards row i of C^-1 is the right half of row i divided by
+// a_ii.  With C^-1 explicit, the solve X = C^-1 B and the correction of the
+// FP64 iterative-refinement step, X += C^-1 (B - C X), are parallel
+// matrix-vector products instead of sequential triangular sweeps, and the
+// code stays a few compact loops (a cold instruction cache is the latency
+// limit of a kernel that runs once per call).
+// ---------------------------------------------------------------------------
+struct GJSmem {
+    static constexpr int LDA = 2 * KRIG_KMAX + 1;  // odd: conflict-free column access
+    float A[KRIG_KMAX * LDA];
+    float Xf[KRIG_KMAX * 8];
+    double Bd[KRIG_KMAX * 8];
+    double Xd[KRIG_KMAX * 8];
+    Tap tap[KRIG_KMAX];
+    int flag;
+};
+
+template <int NT>
+__device__ bool block_gj_solve(GJSmem& S, const LagDims& d, const double* gC, int K, int NC, int tid)
+{
+    constexpr int LDA = GJSmem::LDA;
+    float* A = S.A;
+    for (int e = tid; e < K * K; e += NT) {
+        const int i = e / K, j = e % K;
+        A[i * LDA + j] = (float)krig_cij(d, gC, S.tap[i], S.tap[j]);
+        A[i * LDA + K + j] = (i == j) ? 1.0f : 0.0f;
+    }
+    if (tid == 0) S.flag = 1;
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int k = 0; k < K; ++k) {
+        const float piv = A[k * LDA + k];
+        if (!(piv > 0.0f)) {  // uniform: every thread reads the same pivot
+            if (tid == 0) S.flag = 0;
+            break;
+        }
+        const float ip = 1.0f / piv;
+        // rows over warps, the K columns that can still be nonzero over lanes:
+        // left k+1..K-1, right K..K+k
+        const int nl = K - 1 - k;
+        for (int i = warp; i < K; i += NT / 32) {
+            if (i == k) continue;
+            const float f = A[i * LDA + k] * ip;
+            for (int c = lane; c < K; c += 32) {
+                const int j = c < nl ? k + 1 + c : K + (c - nl);
+                A[i * LDA + j] = fmaf(-f, A[k * LDA + j], A[i * LDA + j]);
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (!S.flag) return false;
+    // C^-1 in place: right half of row i divided by its pivot
+    for (int e = tid; e < K * K; e += NT) {
+        const int i = e / K, j = e % K;
+        A[i * LDA + K + j] *= 1.0f / A[i * LDA + i];
+    }
+    __syncthreads();
+    const float* Ci = A + K;  // C^-1 with leading dimension LDA
+    // X = C^-1 B (FP32), kept in FP64
+    for (int e = tid; e < K * NC; e += NT) {
+        const int i = e / NC, c = e % NC;
+        float s = 0.0f;
+        for (int j = 0; j < K; ++j) s = fmaf(Ci[i * LDA + j], (float)S.Bd[j * 8 + c], s);
+        S.Xd[i * 8 + c] = (double)s;
+    }
+    __syncthreads();
+    // FP64 residual R = B - C X
+    for (int e = tid; e < K * NC; e += NT) {
+        const int i = e / NC, c = e % NC;
+        double s = S.Bd[i * 8 + c];
+        const Tap ti = S.tap[i];
+        for (int j = 0; j < K; ++j) s -= krig_cij(d, gC, ti, S.tap[j]) * S.Xd[j * 8 + c];
+        S.Xf[i * 8 + c] = (float)s;
+    }
+    __syncthreads();
+    // correction X += C^-1 R
+    for (int e = tid; e < K * NC; e += NT) {
+        const int i = e / NC, c = e % NC;
+        float s = 0.0f;
+        for (int j = 0; j < K; ++j) s = fmaf(Ci[i * LDA + j], S.Xf[j * 8 + c], s);
+        S.Xd[i * 8 + c] += (double)s;
+    }
+    __syncthreads();
+    return true;
 }

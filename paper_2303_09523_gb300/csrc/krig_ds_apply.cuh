@@ -1,0 +1,742 @@
+// krig_ds_apply.cuh -- stencil apply of the deduplicated-stencil (DS) form.
+//
+// Every missing voxel (x, y, jg+t) is the weighted sum of the (2r+1)^2
+// windows around (x, y) in known slices j and j+1 (Sec. 4.1.2), with the
+// weights of its truncation class solved by k_ds_solve.  k_ds_apply walks the
+// work items of Algorithm 1: an item is one 64 x 16 in-plane tile of a run of
+// consecutive gaps ("chunk") inside one Z sub-block.  The item's known slices
+// (tile plus halo) stream through a ring of shared-memory slots filled by the
+// TMA bulk-copy engine (cp.async.bulk, completion on an mbarrier), one slice
+// ahead of the compute, so each known slice of the chunk is read from memory
+// once.  The item writes its output slices -- the bit-exact copy of its known
+// slices (Algorithm 1 step 3) and the interpolated ones -- straight to their
+// final offsets (the merge of Sec. 4.2).
+//
+// Interior pixels (full window) use the D4 symmetry of the interior class:
+// the taps of each orbit {same max(|dx|,|dy|), min(|dx|,|dy|)} share one
+// weight, so the stencil is applied to orbit sums (6 per slice for r = 2)
+// instead of 25 taps.  Pixels within r of the slice border take the general
+// path with the full weight row of their own class.  A warp covers a 16 x 8
+// block of pixels (four per thread), so only warps at the border diverge.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "krig_device.cuh"
+
+template <typename TI> struct DsTypes;
+template <> struct DsTypes<double> { typedef double TC; typedef double TO; static constexpr int PAD = 4, RP = 72; };
+template <> struct DsTypes<float> { typedef float TC; typedef float TO; static constexpr int PAD = 8, RP = 80; };
+template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; static constexpr int PAD = 8, RP = 96; };
+// RP (elements per shared row) >= TX + 2 PAD; RP * sizeof is 64 mod 128 bytes so the
+// two rows read by a quarter warp fall in different banks.
+
+#define DS_STAGES 4
+#define DS_CONSUMERS 8  // consumer warps; one more warp produces
+#define DS_BLOCK ((DS_CONSUMERS + 1) * 32)
+#define DS_WAIT_LIMIT (1u << 22)
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld4(const double* p, double o[4])
+{
+    double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, float o[4])
+{
+    float4 a = *(const float4*)p;
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const uint16_t* p, float o[4])
+{
+    uint2 a = *(const uint2*)p;
+    o[0] = (float)(a.x & 0xffffu); o[1] = (float)(a.x >> 16); o[2] = (float)(a.y & 0xffffu); o[3] = (float)(a.y >> 16);
+}
+
+__device__ __forceinline__ void ldw8(const float* p, float w[8])
+{
+    float4 a = *(const float4*)p, b = *(const float4*)(p + 4);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+__device__ __forceinline__ void ldw8(const double* p, double w[8])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double2 a = *(const double2*)(p + 2 * q);
+        w[2 * q] = a.x; w[2 * q + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void ldgw8(const float* p, float w[8])
+{
+    float4 a = __ldg((const float4*)p), b = __ldg((const float4*)(p + 4));
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+__device__ __forceinline__ void ldgw8(const double* p, double w[8])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double2 a = __ldg((const double2*)(p + 2 * q));
+        w[2 * q] = a.x; w[2 * q + 1] = a.y;
+    }
+}
+
+// exact value of a stored input element (u16: float32(u) * scale)
+__device__ __forceinline__ double cvt_out(double x, float) { return x; }
+__device__ __forceinline__ float cvt_out(float x, float) { return x; }
+__device__ __forceinline__ float cvt_out(uint16_t u, float scale) { return __fmul_rn((float)u, scale); }
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T v[4], bool vec_ok, int nvalid)
+{
+    if (vec_ok) {
+        if (sizeof(T) == 4) {
+            __stcs((float4*)p, make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]));
+        } else {
+            __stcs((double2*)p, make_double2((double)v[0], (double)v[1]));
+            __stcs((double2*)p + 1, make_double2((double)v[2], (double)v[3]));
+        }
+    } else {
+        for (int q = 0; q < 4; ++q)
+            if (q < nvalid) p[q] = v[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Slot fill by warp 0: lane i handles shared row i (tile row + halo).  Rows
+// and column ranges outside the slice are zero-filled with ordinary stores
+// (they meet zero weights of truncated taps); the rest arrives by bulk copy.
+// x0 - PAD and W are multiples of the 16-byte chunk, so every copied segment
+// starts and ends on a 16-byte boundary.
+// ---------------------------------------------------------------------------
+template <typename TI, int R>
+__device__ __forceinline__ void ds_issue_fill(TI* slot, uint64_t* bar, const TI* src, int x0, int y0, int H, int W,
+                                              int lane)
+{
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    constexpr int ROWS = KRIG_TY + 2 * R;
+    constexpr int SPAN = KRIG_TX + 2 * PAD;
+    constexpr int VEC = 16 / sizeof(TI);
+    const int xs = x0 - PAD;
+    const int xa = max(xs, 0), xb = min(xs + SPAN, W);
+    const int ya = max(y0 - R, 0), yb = min(y0 + KRIG_TY + R, H);
+    const uint32_t row_bytes = (uint32_t)(xb - xa) * sizeof(TI);
+    const uint32_t total = row_bytes * (uint32_t)(yb - ya);
+    for (int rr = lane; rr < ROWS; rr += 32) {
+        const int yy = y0 - R + rr;
+        TI* row = slot + rr * RP;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        if (yy < ya || yy >= yb) {
+            for (int c = 0; c < SPAN; c += VEC) *(uint4*)(row + c) = z;
+        } else {
+            for (int c = 0; c < xa - xs; c += VEC) *(uint4*)(row + c) = z;
+            for (int c = xb - xs; c < SPAN; c += VEC) *(uint4*)(row + c) = z;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    for (int rr = lane; rr < ROWS; rr += 32) {
+        const int yy = y0 - R + rr;
+        if (yy >= ya && yy < yb && row_bytes)
+            bulk_g2s(slot + rr * RP + (xa - xs), src + (size_t)yy * W + xa, row_bytes, bar);
+    }
+}
+
+// Plain-load fill by the producer warp for slices whose rows are not
+// 16-byte multiples (any W); completion is a plain arrive on the barrier.
+template <typename TI, int R>
+__device__ __forceinline__ void ds_plain_fill(TI* slot, uint64_t* bar, const TI* src, int x0, int y0, int H, int W,
+                                              int lane)
+{
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    constexpr int ROWS = KRIG_TY + 2 * R;
+    constexpr int SPAN = KRIG_TX + 2 * PAD;
+    for (int e = lane; e < ROWS * SPAN; e += 32) {
+        const int rr = e / SPAN, cc = e % SPAN;
+        const int yy = y0 - R + rr, xx = x0 - PAD + cc;
+        TI val = TI(0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) val = src[(size_t)yy * W + xx];
+        slot[rr * RP + cc] = val;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
+// ---------------------------------------------------------------------------
+// Accumulation
+// ---------------------------------------------------------------------------
+
+// General path: full weight row per pixel class, taps from both slices.
+template <typename TI, int R, int GM1>
+__device__ __forceinline__ void ds_accum_general(typename DsTypes<TI>::TC (&acc)[KRIG_PX][GM1 > 0 ? GM1 : 1],
+                                                 const TI* lo, const TI* hi, int lrow, int lcol,
+                                                 const typename DsTypes<TI>::TC* wrow, unsigned mask)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    constexpr int N2R = 2 * R + 1;
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const TI* slot = s == 0 ? lo : hi;
+#pragma unroll 1
+        for (int dy = -R; dy <= R; ++dy) {
+            const TI* rowp = slot + (lrow + R + dy) * RP + PAD + lcol;
+            TC a[4], b[4], c[4];
+            ld4(rowp - 4, a);
+            ld4(rowp, b);
+            ld4(rowp + 4, c);
+            const TC vals[12] = {a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], c[0], c[1], c[2], c[3]};
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                TC w[8];
+                ldgw8(wrow + ((s * N2R + (dy + R)) * N2R + (dx + R)) * KRIG_TSLOTS, w);
+#pragma unroll
+                for (int p = 0; p < KRIG_PX; ++p) {
+                    if (!((mask >> p) & 1u)) continue;
+                    const TC x = vals[4 + p + dx];
+#pragma unroll
+                    for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], x, acc[p][t]);
+                }
+            }
+        }
+    }
+}
+
+// Interior path: orbit sums of each slice times the interior orbit weights.
+// ow: shared [2][KRIG_NORB][8] orbit weights.
+template <typename TI, int R, int GM1>
+__device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc)[KRIG_PX][GM1 > 0 ? GM1 : 1],
+                                                  const TI* lo, const TI* hi, int lrow, int lcol,
+                                                  const typename DsTypes<TI>::TC* ow)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    constexpr int NO = R == 0 ? 1 : (R == 1 ? 3 : 6);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const TI* slot = s == 0 ? lo : hi;
+        // columns 4-R .. 7+R of the 12 loaded around the thread's four pixels
+        TC c0[12], a1[12], a2[12];
+        {
+            const TI* rowp = slot + (lrow + R) * RP + PAD + lcol;
+            TC a[4], b[4], c[4];
+            ld4(rowp - 4, a);
+            ld4(rowp, b);
+            ld4(rowp + 4, c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                c0[q] = a[q];
+                c0[4 + q] = b[q];
+                c0[8 + q] = c[q];
+            }
+        }
+        if (R >= 1) {
+            const TI* rm = slot + (lrow + R - 1) * RP + PAD + lcol;
+            const TI* rp = slot + (lrow + R + 1) * RP + PAD + lcol;
+            TC a[4], b[4], c[4], d[4], e[4], f[4];
+            ld4(rm - 4, a);
+            ld4(rm, b);
+            ld4(rm + 4, c);
+            ld4(rp - 4, d);
+            ld4(rp, e);
+            ld4(rp + 4, f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a1[q] = a[q] + d[q];
+                a1[4 + q] = b[q] + e[q];
+                a1[8 + q] = c[q] + f[q];
+            }
+        }
+        if (R >= 2) {
+            const TI* rm = slot + (lrow + R - 2) * RP + PAD + lcol;
+            const TI* rp = slot + (lrow + R + 2) * RP + PAD + lcol;
+            TC a[4], b[4], c[4], d[4], e[4], f[4];
+            ld4(rm - 4, a);
+            ld4(rm, b);
+            ld4(rm + 4, c);
+            ld4(rp - 4, d);
+            ld4(rp, e);
+            ld4(rp + 4, f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a2[q] = a[q] + d[q];
+                a2[4 + q] = b[q] + e[q];
+                a2[8 + q] = c[q] + f[q];
+            }
+        }
+        TC orb[KRIG_PX][NO];
+#pragma unroll
+        for (int p = 0; p < KRIG_PX; ++p) {
+            const int m = 4 + p;  // centre column
+            orb[p][0] = c0[m];
+            if (R >= 1) {
+                orb[p][1] = (c0[m - 1] + c0[m + 1]) + a1[m];
+                orb[p][2] = a1[m - 1] + a1[m + 1];
+            }
+            if (R >= 2) {
+                orb[p][3] = (c0[m - 2] + c0[m + 2]) + a2[m];
+                orb[p][4] = (a1[m - 2] + a1[m + 2]) + (a2[m - 1] + a2[m + 1]);
+                orb[p][5] = a2[m - 2] + a2[m + 2];
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            TC w[8];
+            ldgw8(ow + (s * KRIG_NORB + o) * KRIG_TSLOTS, w);
+#pragma unroll
+            for (int p = 0; p < KRIG_PX; ++p)
+#pragma unroll
+                for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], orb[p][o], acc[p][t]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent producer / consumer pipeline
+//
+// Blocks walk the work items round-robin.  Warp DS_CONSUMERS is the producer:
+// it streams every known slice the block needs, item after item, into a ring
+// of DS_STAGES slots ("full" barrier per slot, completed by the bulk copy),
+// after the consumers released the slot's previous slice ("empty" barrier,
+// one arrival per consumer warp).  The consumer warps compute gap after gap;
+// they never wait on each other.  Every wait is bounded; a wait that gives up
+// sets the device status KRIG_DEV_TIMEOUT and the shared abort flag, and the
+// producer then waits (bounded) for the copies it still has in flight.
+// ---------------------------------------------------------------------------
+struct DsItem {
+    int v, x0, y0, c0, c1;
+};
+
+__device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype, DsItem& d)
+{
+    int v = 0;
+    for (int u = 1; u < P.n_vols; ++u)
+        if (P.vol[u].item_begin <= it) v = u;
+    const KrigVol& V = P.vol[v];
+    if (V.dtype != dtype) return false;
+    const int local = it - (int)V.item_begin;
+    const int tiles = V.tiles_x * V.tiles_y;
+    const int tile = local % tiles, rest = local / tiles;
+    const int ch = rest % V.chunks, b = rest / V.chunks;
+    const int G = V.n - 1, q = G / V.k, rm = G % V.k;
+    const int a0 = b * q + min(b, rm), a1 = (b + 1) * q + min(b + 1, rm);
+    d.v = v;
+    d.c0 = a0 + ch * V.chunk;
+    d.c1 = min(d.c0 + V.chunk, a1);
+    d.x0 = (tile % V.tiles_x) * KRIG_TX;
+    d.y0 = (tile / V.tiles_x) * KRIG_TY;
+    return d.c0 < d.c1;
+}
+
+struct DsShared {
+    uint64_t* full;
+    uint64_t* empty;
+    uint64_t* never;  // test hook: a barrier nothing completes
+    int* abort;
+};
+
+// One gap of one item for the consumer warps: passthrough of known slice j
+// for every pixel, and the g-1 interpolated slices (with variance) for the
+// interior pixels, through the orbit sums.  Frame pixels (within r of the
+// border) are written by the frame units instead.
+template <typename TI, int R, int GM1>
+__device__ __forceinline__ void ds_gap(const KrigLaunch& P, const KrigVol& V, int v, const DsItem& d, int j,
+                                       const TI* lo, const TI* hi, int lrow, int lcol)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    typedef typename DsTypes<TI>::TO TO;
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    const int H = V.H, W = V.W, g = V.g;
+    const int64_t plane = (int64_t)H * W;
+    const int y = d.y0 + lrow, xb = d.x0 + lcol;
+    const int nvalid = min(KRIG_PX, W - xb);
+    if (y >= H || nvalid <= 0) return;
+    const bool vec_out = (W % KRIG_PX == 0) && nvalid == KRIG_PX;
+    TO* out = (TO*)P.out[v];
+    float* var = P.var[v];
+    const int64_t pix = (int64_t)y * W + xb;
+    {   // known slice j -> output slice j*g, bit-exact
+        TO kv[4];
+        const TI* cptr = lo + (lrow + R) * RP + PAD + lcol;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(cptr[p], V.scale);
+        st4<TO>(out + (int64_t)j * g * plane + pix, kv, vec_out, nvalid);
+        if (var) {
+            const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+            st4<float>(var + (int64_t)j * g * plane + pix, z4, vec_out, nvalid);
+        }
+        if (j == V.n - 2) {  // the volume's last known slice
+            const TI* ch_ = hi + (lrow + R) * RP + PAD + lcol;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(ch_[p], V.scale);
+            st4<TO>(out + (int64_t)(j + 1) * g * plane + pix, kv, vec_out, nvalid);
+            if (var) {
+                const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+                st4<float>(var + (int64_t)(j + 1) * g * plane + pix, z4, vec_out, nvalid);
+            }
+        }
+    }
+    if constexpr (GM1 == 0) {
+        return;
+    } else {
+        if (V.cint < 0 || y < R || y > H - 1 - R) return;  // no interior pixel in this row
+        // interior pixels of the four: x in [R, W-1-R]
+        const int plo = max(0, R - xb), phi = min(nvalid, W - R - xb);  // [plo, phi)
+        if (plo >= phi) return;
+        TC acc[KRIG_PX][GM1];
+#pragma unroll
+        for (int p = 0; p < KRIG_PX; ++p)
+#pragma unroll
+            for (int t = 0; t < GM1; ++t) acc[p][t] = TC(0);
+        ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, (const TC*)(P.ws + V.otab_off));
+        const bool full = vec_out && plo == 0 && phi == KRIG_PX;
+        const float vint = 0.0f;
+        const float* vt = (const float*)(P.ws + V.vtab_off) + (int64_t)V.cint * KRIG_TSLOTS;
+        (void)vint;
+#pragma unroll
+        for (int t = 0; t < GM1; ++t) {
+            TO o[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][t];
+            TO* dst = out + ((int64_t)j * g + t + 1) * plane + pix;
+            float* vdst = var ? var + ((int64_t)j * g + t + 1) * plane + pix : nullptr;
+            if (full) {
+                st4<TO>(dst, o, true, 4);
+                if (vdst) {
+                    const float vv = vt[t];
+                    const float v4[4] = {vv, vv, vv, vv};
+                    st4<float>(vdst, v4, true, 4);
+                }
+            } else {
+                for (int p = plo; p < phi; ++p) {
+                    dst[p] = o[p];
+                    if (vdst) vdst[p] = vt[t];
+                }
+            }
+        }
+    }
+}
+
+// Frame unit: 32 frame pixels of one gap, one lane each, full weight row of
+// the pixel's own truncation class; taps read from global memory (L2).
+__device__ __forceinline__ void ds_frame_pixel(const KrigVol& V, int f, int* x, int* y)
+{
+    const int r = V.r, W = V.W, H = V.H;
+    if (V.cint < 0) {
+        *x = f % W;
+        *y = f / W;
+    } else if (f < r * W) {
+        *x = f % W;
+        *y = f / W;
+    } else if (f < 2 * r * W) {
+        f -= r * W;
+        *x = f % W;
+        *y = H - r + f / W;
+    } else {
+        f -= 2 * r * W;
+        const int c = f % (2 * r);
+        *y = r + f / (2 * r);
+        *x = c < r ? c : W - 2 * r + c;
+    }
+}
+
+template <typename TI, int GM1>
+__device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, int f0, int lane)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    typedef typename DsTypes<TI>::TO TO;
+    const KrigVol& V = P.vol[v];
+    const int f = f0 + lane;
+    if (f >= V.n_frame) return;
+    int x, y;
+    ds_frame_pixel(V, f, &x, &y);
+    const int r = V.r, W = V.W, H = V.H, g = V.g;
+    const int n2r = 2 * r + 1;
+    const int64_t plane = (int64_t)H * W;
+    const int cy = V.ymap[krig_slot(y, H, r)], cx = V.xmap[krig_slot(x, W, r)];
+    const TC* wrow = (const TC*)(P.ws + V.wtab_off) + ((int64_t)cy * V.ncx + cx) * (2 * n2r * n2r) * KRIG_TSLOTS;
+    const TI* in = (const TI*)P.in[v];
+    TC acc[GM1];
+#pragma unroll
+    for (int t = 0; t < GM1; ++t) acc[t] = TC(0);
+    for (int s = 0; s < 2; ++s) {
+        const TI* sl = in + (size_t)(j + s) * plane;
+        for (int dy = -r; dy <= r; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -r; dx <= r; ++dx) {
+                const int xx = x + dx;
+                if (xx < 0 || xx >= W) continue;
+                TC w[8];
+                ldgw8(wrow + ((s * n2r + (dy + r)) * n2r + (dx + r)) * KRIG_TSLOTS, w);
+                TC z;
+                if constexpr (sizeof(TI) == 2) z = (TC)sl[(size_t)yy * W + xx];  // weights carry the u16 scale
+                else z = (TC)sl[(size_t)yy * W + xx];
+#pragma unroll
+                for (int t = 0; t < GM1; ++t) acc[t] = fma(w[t], z, acc[t]);
+            }
+        }
+    }
+    TO* out = (TO*)P.out[v];
+    float* var = P.var[v];
+    const float* vt = (const float*)(P.ws + V.vtab_off) + ((int64_t)cy * V.ncx + cx) * KRIG_TSLOTS;
+    const int64_t pix = (int64_t)y * W + x;
+#pragma unroll
+    for (int t = 0; t < GM1; ++t) {
+        out[((int64_t)j * g + t + 1) * plane + pix] = (TO)acc[t];
+        if (var) var[((int64_t)j * g + t + 1) * plane + pix] = vt[t];
+    }
+}
+
+template <typename TI>
+__device__ __forceinline__ void ds_frame_dispatch(const KrigLaunch& P, int v, int j, int f0, int lane)
+{
+    switch (P.vol[v].g) {
+    case 2: ds_frame_unit<TI, 1>(P, v, j, f0, lane); break;
+    case 3: ds_frame_unit<TI, 2>(P, v, j, f0, lane); break;
+    case 4: ds_frame_unit<TI, 3>(P, v, j, f0, lane); break;
+    case 5: ds_frame_unit<TI, 4>(P, v, j, f0, lane); break;
+    case 6: ds_frame_unit<TI, 5>(P, v, j, f0, lane); break;
+    case 7: ds_frame_unit<TI, 6>(P, v, j, f0, lane); break;
+    case 8: ds_frame_unit<TI, 7>(P, v, j, f0, lane); break;
+    default: break;  // g = 1: nothing to interpolate
+    }
+}
+
+template <typename TI, int R, int GM1>
+__device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
+                                             const DsShared& sh, int warp, int lane)
+{
+    const KrigVol& V = P.vol[d.v];
+    const int lrow = (warp >> 2) * 8 + (lane >> 2);
+    const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
+    const int nsl = d.c1 - d.c0 + 1;
+    bool ok = mbar_wait(&sh.full[q % DS_STAGES], (q / DS_STAGES) & 1, DS_WAIT_LIMIT);
+    for (int m = 0; m + 1 < nsl && ok; ++m) {
+        const int ql = q + m, qh = q + m + 1;
+        ok = mbar_wait(&sh.full[qh % DS_STAGES], (qh / DS_STAGES) & 1, DS_WAIT_LIMIT);
+        if (!ok) break;
+        ds_gap<TI, R, GM1>(P, V, d.v, d, d.c0 + m, slots + (ql % DS_STAGES) * stride,
+                           slots + (qh % DS_STAGES) * stride, lrow, lcol);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.empty[ql % DS_STAGES]);
+    }
+    __syncwarp();
+    if (ok) {
+        if (lane == 0) mbar_arrive(&sh.empty[(q + nsl - 1) % DS_STAGES]);
+    } else {
+        if (lane == 0) {
+            krig_set_status(P.status, KRIG_DEV_TIMEOUT);
+            atomicExch(sh.abort, 1);
+        }
+    }
+}
+
+template <typename TI, int R>
+__device__ __forceinline__ void ds_consume_g(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
+                                             const DsShared& sh, int warp, int lane)
+{
+    switch (P.vol[d.v].g) {
+    case 1: ds_consume_item<TI, R, 0>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 2: ds_consume_item<TI, R, 1>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 3: ds_consume_item<TI, R, 2>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 4: ds_consume_item<TI, R, 3>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 5: ds_consume_item<TI, R, 4>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 6: ds_consume_item<TI, R, 5>(P, d, q, slots, stride, sh, warp, lane); break;
+    case 7: ds_consume_item<TI, R, 6>(P, d, q, slots, stride, sh, warp, lane); break;
+    default: ds_consume_item<TI, R, 7>(P, d, q, slots, stride, sh, warp, lane); break;
+    }
+}
+
+template <typename TI>
+__device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in, const DsItem& d, int s, TI* slot,
+                                                 uint64_t* bar, int lane)
+{
+    const int64_t plane = (int64_t)V.H * V.W;
+    const TI* src = in + (size_t)s * plane;
+    const bool bulk = (V.W % (16 / (int)sizeof(TI))) == 0;
+    switch (V.r) {
+    case 0:
+        if (bulk) ds_issue_fill<TI, 0>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        else ds_plain_fill<TI, 0>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        break;
+    case 1:
+        if (bulk) ds_issue_fill<TI, 1>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        else ds_plain_fill<TI, 1>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        break;
+    default:
+        if (bulk) ds_issue_fill<TI, 2>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        else ds_plain_fill<TI, 2>(slot, bar, src, d.x0, d.y0, V.H, V.W, lane);
+        break;
+    }
+}
+
+// One kernel per input type (compiled in separate translation units); items
+// of volumes of another type are skipped.
+template <typename TI>
+__global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int RP = DsTypes<TI>::RP;
+    constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * RP;  // slot stride, elements
+    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    TI* slots = (TI*)sm;
+    uint64_t* bars = (uint64_t*)(sm + (size_t)DS_STAGES * stride * sizeof(TI));
+    DsShared sh{bars, bars + DS_STAGES, bars + 2 * DS_STAGES, (int*)(bars + 2 * DS_STAGES + 1)};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < DS_STAGES) {
+        mbar_init(&sh.full[tid], 1);
+        mbar_init(&sh.empty[tid], DS_CONSUMERS);
+    }
+    if (tid == 0) {
+        mbar_init(sh.never, 1);
+        *sh.abort = 0;
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    const int n_items = (int)P.n_items;
+    if (warp == DS_CONSUMERS) {
+        // ---------------- producer warp
+        int q = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            DsItem d;
+            if (!ds_decode(P, it, dtype, d)) continue;
+            const KrigVol& V = P.vol[d.v];
+            for (int s = d.c0; s <= d.c1; ++s, ++q) {
+                const int slot = q % DS_STAGES;
+                if (q >= DS_STAGES && !mbar_wait(&sh.empty[slot], ((q / DS_STAGES) - 1) & 1, DS_WAIT_LIMIT)) {
+                    ok = false;
+                    break;
+                }
+                if (*(volatile int*)sh.abort) {
+                    ok = false;
+                    break;
+                }
+                fence_proxy_async_smem();
+                ds_produce_slice<TI>(V, (const TI*)P.in[d.v], d, s, slots + slot * stride, &sh.full[slot], lane);
+            }
+        }
+        if (!ok) {
+            if (lane == 0) {
+                krig_set_status(P.status, KRIG_DEV_TIMEOUT);
+                atomicExch(sh.abort, 1);
+            }
+            // bounded wait for the copies still in flight (the last DS_STAGES issued)
+            for (int qq = max(0, q - DS_STAGES); qq < q; ++qq)
+                mbar_wait(&sh.full[qq % DS_STAGES], (qq / DS_STAGES) & 1, DS_WAIT_LIMIT);
+        }
+        return;
+    }
+    // ---------------- consumer warps
+    if (P.fault_timeout && blockIdx.x == 0 && warp == 0) {
+        // test hook: wait on a barrier nothing completes; the bounded wait gives up
+        if (!mbar_wait(sh.never, 0, 1u << 12) && lane == 0) {
+            krig_set_status(P.status, KRIG_DEV_TIMEOUT);
+            atomicExch(sh.abort, 1);
+        }
+    }
+    int q = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        DsItem d;
+        if (!ds_decode(P, it, dtype, d)) continue;
+        if (*(volatile int*)sh.abort) break;
+        switch (P.vol[d.v].r) {
+        case 0: ds_consume_g<TI, 0>(P, d, q, slots, stride, sh, warp, lane); break;
+        case 1: ds_consume_g<TI, 1>(P, d, q, slots, stride, sh, warp, lane); break;
+        default: ds_consume_g<TI, 2>(P, d, q, slots, stride, sh, warp, lane); break;
+        }
+        q += d.c1 - d.c0 + 1;
+    }
+    // frame units, spread over every consumer warp of the grid
+    if (*(volatile int*)sh.abort) return;
+    const int64_t nfu = P.n_frame_units;
+    for (int64_t u = (int64_t)blockIdx.x * DS_CONSUMERS + warp; u < nfu; u += (int64_t)gridDim.x * DS_CONSUMERS) {
+        int v = 0;
+        for (int w = 1; w < P.n_vols; ++w)
+            if (P.vol[w].frame_begin <= u) v = w;
+        const KrigVol& V = P.vol[v];
+        if (V.dtype != dtype || V.frame_units == 0) continue;
+        const int64_t lu = u - V.frame_begin;
+        const int j = (int)(lu / V.frame_units);
+        const int f0 = (int)(lu % V.frame_units) * 32;
+        ds_frame_dispatch<TI>(P, v, j, f0, lane);
+    }
+}
+
+template <typename TI>
+int krig_launch_ds_apply_t(const KrigLaunch& L, cudaStream_t st)
+{
+    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    bool any = false;
+    for (int v = 0; v < L.n_vols; ++v) any = any || L.vol[v].dtype == dtype;
+    if (!any) return 0;
+    constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;
+    const size_t smem = (size_t)DS_STAGES * stride * sizeof(TI) + (2 * DS_STAGES + 2) * sizeof(uint64_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_ds_apply<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ds_apply<TI>, DS_BLOCK, smem);
+    if (e != cudaSuccess) return (int)e;
+    const int sms = krig_device_sm_count();
+    int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (grid > L.n_items) grid = L.n_items;
+    k_ds_apply<TI><<<(unsigned)grid, DS_BLOCK, smem, st>>>(L);
+    return (int)cudaGetLastError();
+}

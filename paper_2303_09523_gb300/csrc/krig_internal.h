@@ -40,6 +40,14 @@ struct KrigVol {
     int64_t wtab_off;         // byte offset of the DS weight table in the workspace
     int64_t vtab_off;         // byte offset of the DS variance table in the workspace
     int64_t lag_off;          // byte offset of the FP64 lag tables (per-voxel forms)
+    int64_t otab_off;         // byte offset of the interior-class orbit weights [2][6][8] (DS)
+    int32_t chunk;            // gaps per DS work item (a sub-block is cut into chunks)
+    int32_t chunks;           // chunks per sub-block
+    int32_t cint;             // interior xy-class index, or -1 if the slice is narrower than 2r+1
+    int32_t n_frame;          // frame pixels (within r of the border) per slice (DS)
+    int64_t frame_begin;      // first DS frame unit (32 frame pixels of one gap) of this volume
+    int32_t frame_units;      // frame units per gap
+    int32_t pad0;
 };
 
 struct KrigLaunch {
@@ -55,6 +63,9 @@ struct KrigLaunch {
     int64_t n_items;            // DS work items over all volumes
     int64_t n_classes;          // xy-classes over all volumes
     int64_t n_vox;              // output voxels over all volumes
+    int64_t n_frame_units;      // DS frame units over all volumes
+    int32_t fault_timeout;      // test only: make one bounded device wait give up
+    int32_t pad0;
 };
 
 // Kernel launchers (krig_ds.cu, krig_voxel.cu). Return cudaError_t as int.
@@ -74,7 +85,94 @@ inline int64_t krig_wtab_bytes(const KrigVol& v)
     return (int64_t)v.ncx * v.ncy * taps * KRIG_TSLOTS * esz;
 }
 inline int64_t krig_vtab_bytes(const KrigVol& v) { return (int64_t)v.ncx * v.ncy * KRIG_TSLOTS * 4; }
+#define KRIG_NORB 6  // D4 orbits of a (2r+1)^2 window for r <= 2
+inline int64_t krig_otab_bytes(const KrigVol& v) { return 2LL * KRIG_NORB * KRIG_TSLOTS * (v.dtype == KRIG_F64 ? 8 : 4); }
 inline int64_t krig_lag_bytes(const KrigVol& v)
 {
     return 8LL * (2 * (2 * v.r + 1) * (2 * v.r + 1) + (v.g > 1 ? v.g - 1 : 0) * 2 * (v.r + 1) * (v.r + 1));
+}
+
+// Truncation classes along one axis of length N for half-width r: slot
+// l*(r+1)+rr (window p-l .. p+rr) -> compact class, in increasing position.
+inline void krig_axis_classes(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
+{
+    int n = 0;
+    for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) map[i] = -1;
+    for (int p = 0; p < N; ++p) {
+        if (p > r && p < N - r - 1) continue;  // interior positions repeat the class at p = r
+        const int l = p < r ? p : r, rr = (N - 1 - p) < r ? (N - 1 - p) : r;
+        const int slot = l * (r + 1) + rr;
+        if (map[slot] < 0) {
+            map[slot] = (int8_t)n;
+            ext[n][0] = (int8_t)l;
+            ext[n][1] = (int8_t)rr;
+            ++n;
+        }
+    }
+    *count = n;
+}
+
+// Fill the descriptor of one volume and lay its tables out in the workspace
+// from byte offset *off (advanced, 256-byte aligned).  item/class/voxel
+// counters are advanced too.  chunk = gaps per DS work item.
+inline void krig_fill_vol(KrigVol& V, const krig_volume_desc& d, int form, int chunk, int64_t* off, int64_t* items,
+                          int64_t* classes, int64_t* vox, int64_t* frame_units)
+{
+    V.H = d.H;
+    V.W = d.W;
+    V.n = d.n_known;
+    V.g = d.zfactor;
+    V.k = d.n_sub_blocks;
+    V.r = d.half_w;
+    V.dtype = d.in_dtype;
+    V.scale = d.in_dtype == KRIG_U16 ? d.in_scale : 1.0f;
+    krig_axis_classes(d.W, d.half_w, V.xmap, V.xext, &V.ncx);
+    krig_axis_classes(d.H, d.half_w, V.ymap, V.yext, &V.ncy);
+    const int islot = V.r * (V.r + 1) + V.r;
+    V.cint = (V.xmap[islot] >= 0 && V.ymap[islot] >= 0) ? V.ymap[islot] * V.ncx + V.xmap[islot] : -1;
+    // frame: pixels within r of the border (all pixels if there is no interior)
+    if (V.cint < 0) V.n_frame = V.H * V.W;
+    else V.n_frame = 2 * V.r * V.W + 2 * V.r * (V.H - 2 * V.r);
+    V.frame_units = V.g >= 2 ? (V.n_frame + 31) / 32 : 0;
+    V.frame_begin = *frame_units;
+    *frame_units += (int64_t)(V.n - 1) * V.frame_units;
+    V.tiles_x = (d.W + KRIG_TX - 1) / KRIG_TX;
+    V.tiles_y = (d.H + KRIG_TY - 1) / KRIG_TY;
+    const int gaps = V.n - 1;
+    const int max_block = (gaps + V.k - 1) / V.k;
+    V.chunk = chunk < 1 ? 1 : (chunk > max_block ? max_block : chunk);
+    V.chunks = (max_block + V.chunk - 1) / V.chunk;
+    V.item_begin = *items;
+    *items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
+    V.cls_begin = *classes;
+    if (V.g >= 2) *classes += (int64_t)V.ncx * V.ncy;
+    V.vox_begin = *vox;
+    *vox += ((int64_t)(V.n - 1) * V.g + 1) * V.H * V.W;
+    const auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+    V.wtab_off = V.vtab_off = V.lag_off = V.otab_off = 0;
+    if (form == KRIG_FORM_DS) {
+        V.wtab_off = *off;
+        *off = up(*off + krig_wtab_bytes(V));
+        V.vtab_off = *off;
+        *off = up(*off + krig_vtab_bytes(V));
+        V.otab_off = *off;
+        *off = up(*off + krig_otab_bytes(V));
+    } else {
+        V.lag_off = *off;
+        *off = up(*off + krig_lag_bytes(V));
+    }
+    V.pad0 = 0;
+}
+
+// Gaps per DS work item: enough items to keep every SM busy several times
+// over, each item still covering as many gaps as possible.
+inline int krig_pick_chunk(const krig_volume_desc* vols, int n_vols)
+{
+    int64_t gap_tiles = 0;
+    for (int i = 0; i < n_vols; ++i)
+        gap_tiles += (int64_t)(vols[i].n_known - 1) * ((vols[i].W + KRIG_TX - 1) / KRIG_TX) *
+                     ((vols[i].H + KRIG_TY - 1) / KRIG_TY);
+    const int64_t target = 2048;
+    int64_t c = (gap_tiles + target - 1) / target;
+    return (int)(c < 1 ? 1 : c);
 }

@@ -59,25 +59,6 @@ krig_status noalloc_scratch(void** out)
     return KRIG_OK;
 }
 
-// Truncation classes along one axis (no heap use).
-void noalloc_axis(int N, int r, int8_t* map, int8_t (*ext)[2], int* count)
-{
-    int n = 0;
-    for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) map[i] = -1;
-    for (int p = 0; p < N; ++p) {
-        if (p > r && p < N - r - 1) continue;  // interior positions repeat the class at p = r
-        int l = p < r ? p : r, rr = (N - 1 - p) < r ? (N - 1 - p) : r;
-        int slot = l * (r + 1) + rr;
-        if (map[slot] < 0) {
-            map[slot] = (int8_t)n;
-            ext[n][0] = (int8_t)l;
-            ext[n][1] = (int8_t)rr;
-            ++n;
-        }
-    }
-    *count = n;
-}
-
 }  // namespace
 
 extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out,
@@ -103,32 +84,17 @@ extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, co
     L.n_vols = 1;
     L.form = KRIG_FORM_DS;
     KrigVol& V = L.vol[0];
-    V.H = d.H;
-    V.W = d.W;
-    V.n = d.n_known;
-    V.g = d.zfactor;
-    V.k = d.n_sub_blocks;
-    V.r = d.half_w;
-    V.dtype = d.in_dtype;
-    V.scale = d.in_dtype == KRIG_U16 ? d.in_scale : 1.0f;
-    noalloc_axis(d.W, d.half_w, V.xmap, V.xext, &V.ncx);
-    noalloc_axis(d.H, d.half_w, V.ymap, V.yext, &V.ncy);
-    V.tiles_x = (d.W + KRIG_TX - 1) / KRIG_TX;
-    V.tiles_y = (d.H + KRIG_TY - 1) / KRIG_TY;
-    V.item_begin = 0;
-    V.cls_begin = 0;
-    V.vox_begin = 0;
-    V.wtab_off = 256;
-    V.vtab_off = (V.wtab_off + krig_wtab_bytes(V) + 255) / 256 * 256;
-    const int64_t need = (V.vtab_off + krig_vtab_bytes(V) + 255) / 256 * 256;
+    int64_t need = 256, items = 0, classes = 0, vox = 0, frames = 0;
+    krig_fill_vol(V, d, KRIG_FORM_DS, krig_pick_chunk(&d, 1), &need, &items, &classes, &vox, &frames);
+    L.n_frame_units = frames;
     if (need > KRIG_NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(KRIG_EINVAL, "this volume needs " + std::to_string((long long)need) +
                                              " bytes of scratch; the static scratch holds " +
                                              std::to_string(KRIG_NOALLOC_SCRATCH_BYTES) +
                                              " (use krig_plan_create with a caller workspace instead)");
-    L.n_items = (int64_t)V.k * V.tiles_x * V.tiles_y;
-    L.n_classes = V.g >= 2 ? (int64_t)V.ncx * V.ncy : 0;
-    L.n_vox = ((int64_t)(V.n - 1) * V.g + 1) * V.H * V.W;
+    L.n_items = items;
+    L.n_classes = classes;
+    L.n_vox = vox;
 
     void* scratch = nullptr;
     krig_status st = noalloc_scratch(&scratch);

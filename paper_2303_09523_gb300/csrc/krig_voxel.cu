@@ -33,13 +33,69 @@ __device__ __forceinline__ double in_value(const void* in, int dtype, float scal
     return (double)__fmul_rn((float)((const uint16_t*)in)[idx], scale);
 }
 
+// Register factorisation for PMX at every size and for P64 up to 18 points;
+// the FP64 50-point factor (200 registers) stays in shared memory.
 template <typename TF, int KM>
+struct VoxKind {
+    static constexpr bool REG = sizeof(TF) == 4 || KM <= 18;
+};
+
+template <typename TF, int KM, bool REG>
+struct VoxSmemSel;
+template <typename TF, int KM>
+struct VoxSmemSel<TF, KM, true> { typedef VoxSmem<KM, TF> type; };
+template <typename TF, int KM>
+struct VoxSmemSel<TF, KM, false> { typedef SolveSmem<TF, KM, 2> type; };
+
+template <typename TF, int KM>
+using VoxSmemT = typename VoxSmemSel<TF, KM, VoxKind<TF, KM>::REG>::type;
+
+template <typename TF, int RMAX>
+struct VoxSmemMax {
+    static constexpr size_t s2 = sizeof(VoxSmemT<TF, 2>);
+    static constexpr size_t s18 = RMAX >= 1 ? sizeof(VoxSmemT<TF, 18>) : 0;
+    static constexpr size_t s50 = RMAX >= 2 ? sizeof(VoxSmemT<TF, 50>) : 0;
+    static constexpr size_t m1 = s2 > s18 ? s2 : s18;
+    static constexpr size_t bytes = ((m1 > s50 ? m1 : s50) + 15) / 16 * 16;
+};
+
+// Solve one voxel's system with the solver for its window size KM; S.Xd gets
+// u and v.  The solver depends only on the voxel's own half-width, so a voxel
+// gives the same bits whatever other volumes share the launch.
+template <typename TF, int KM>
+__device__ __forceinline__ bool voxel_solve(unsigned char* raw, const LagDims& d, const double* gC, const double* g0,
+                                            int t, int lx, int rx, int ly, int ry, int lane, Tap** tap_out,
+                                            double** bd_out, double** xd_out)
+{
+    typedef VoxSmemT<TF, KM> Smem;
+    Smem& S = *(Smem*)raw;
+    const int nx = lx + rx + 1, ny = ly + ry + 1;
+    const int K = 2 * nx * ny;
+    __syncwarp();
+    for (int i = lane; i < K; i += 32) {
+        Tap tp;
+        tp.s = (int8_t)(i / (nx * ny));
+        tp.dy = (int8_t)((i / nx) % ny - ly);
+        tp.dx = (int8_t)(i % nx - lx);
+        tp.pad = 0;
+        S.tap[i] = tp;
+        S.Bd[i * 2 + 0] = __ldg(g0 + d.i0(t, tp.s, abs((int)tp.dy), abs((int)tp.dx)));
+        S.Bd[i * 2 + 1] = 1.0;
+    }
+    __syncwarp();
+    *tap_out = S.tap;
+    *bd_out = S.Bd;
+    *xd_out = S.Xd;
+    if constexpr (VoxKind<TF, KM>::REG) return warp_ok_solve_vox<KM, TF>(S, d, gC, K, lane);
+    else return team_ok_solve<TF, KM, 2, 32>(S, d, gC, K, 2, lane);
+}
+
+template <typename TF, int RMAX>
 __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunch P)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    typedef SolveSmem<TF, KM, 2> Smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Smem& S = ((Smem*)smraw)[warp];
+    unsigned char* raw = smraw + (size_t)warp * VoxSmemMax<TF, RMAX>::bytes;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t vox = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; vox < P.n_vox; vox += nwarps) {
         const int v = krig_find_vol(P, vox, 2);
@@ -65,27 +121,19 @@ __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunc
         const double* gC = (const double*)(P.ws + V.lag_off);
         const double* g0 = gC + d.nC();
         const int lx = min(x, r), rx = min(V.W - 1 - x, r), ly = min(y, r), ry = min(V.H - 1 - y, r);
-        const int nx = lx + rx + 1, ny = ly + ry + 1;
-        const int K = 2 * nx * ny;
-        __syncwarp();
-        for (int i = lane; i < K; i += 32) {
-            Tap tp;
-            tp.s = (int8_t)(i / (nx * ny));
-            tp.dy = (int8_t)((i / nx) % ny - ly);
-            tp.dx = (int8_t)(i % nx - lx);
-            tp.pad = 0;
-            S.tap[i] = tp;
-            S.Bd[i * 2 + 0] = __ldg(g0 + d.i0(t, tp.s, abs((int)tp.dy), abs((int)tp.dx)));
-            S.Bd[i * 2 + 1] = 1.0;
-        }
-        __syncwarp();
-        const bool ok = team_ok_solve<TF, KM, 2, 32>(S, d, gC, K, 2, lane);
+        const int K = 2 * (lx + rx + 1) * (ly + ry + 1);
+        Tap* tap;
+        double *Bd, *Xd;
+        bool ok;
+        if (RMAX == 0 || r == 0) ok = voxel_solve<TF, 2>(raw, d, gC, g0, t, lx, rx, ly, ry, lane, &tap, &Bd, &Xd);
+        else if (RMAX == 1 || r == 1) ok = voxel_solve<TF, 18>(raw, d, gC, g0, t, lx, rx, ly, ry, lane, &tap, &Bd, &Xd);
+        else ok = voxel_solve<TF, (RMAX >= 2 ? 50 : 18)>(raw, d, gC, g0, t, lx, rx, ly, ry, lane, &tap, &Bd, &Xd);
         double est = 0.0, var = 0.0;
         if (ok) {
             double su = 0.0, sv = 0.0;
             for (int i = lane; i < K; i += 32) {
-                su += S.Xd[i * 2 + 0];
-                sv += S.Xd[i * 2 + 1];
+                su += Xd[i * 2 + 0];
+                sv += Xd[i * 2 + 1];
             }
             for (int o = 16; o; o >>= 1) {
                 su += __shfl_xor_sync(0xffffffffu, su, o);
@@ -94,11 +142,11 @@ __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunc
             const double phi = (su - 1.0) / sv;
             double wz = 0.0, wc = 0.0;
             for (int i = lane; i < K; i += 32) {
-                Tap tp = S.tap[i];
-                double w = S.Xd[i * 2 + 0] - phi * S.Xd[i * 2 + 1];
+                Tap tp = tap[i];
+                double w = Xd[i * 2 + 0] - phi * Xd[i * 2 + 1];
                 int64_t idx = (int64_t)(j + tp.s) * plane + (int64_t)(y + tp.dy) * V.W + (x + tp.dx);
                 wz += w * in_value(P.in[v], V.dtype, V.scale, idx);
-                wc += w * S.Bd[i * 2 + 0];
+                wc += w * Bd[i * 2 + 0];
             }
             for (int o = 16; o; o >>= 1) {
                 wz += __shfl_xor_sync(0xffffffffu, wz, o);
@@ -118,23 +166,23 @@ __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunc
     }
 }
 
-template <typename TF, int KM>
+template <typename TF, int RMAX>
 static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st)
 {
-    const size_t smem = 8 * sizeof(SolveSmem<TF, KM, 2>);
+    const size_t smem = 8 * VoxSmemMax<TF, RMAX>::bytes;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_voxel<TF, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_voxel<TF, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxel<TF, KM>, 256, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxel<TF, RMAX>, 256, smem);
     if (e != cudaSuccess) return (int)e;
     int sms = krig_device_sm_count();
     int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     int64_t need = (L.n_vox + 7) / 8;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_voxel<TF, KM><<<(unsigned)grid, 256, smem, st>>>(L);
+    k_voxel<TF, RMAX><<<(unsigned)grid, 256, smem, st>>>(L);
     return (int)cudaGetLastError();
 }
 
@@ -148,7 +196,7 @@ int krig_launch_voxel(const KrigLaunch& L, int form, void* stream)
     int rmax = 0;
     for (int v = 0; v < L.n_vols; ++v) rmax = L.vol[v].r > rmax ? L.vol[v].r : rmax;
     const bool fp64 = form == KRIG_FORM_P64;
-    if (rmax == 0) return fp64 ? launch_voxel_t<double, 2>(L, st) : launch_voxel_t<float, 2>(L, st);
-    if (rmax == 1) return fp64 ? launch_voxel_t<double, 18>(L, st) : launch_voxel_t<float, 18>(L, st);
-    return fp64 ? launch_voxel_t<double, 50>(L, st) : launch_voxel_t<float, 50>(L, st);
+    if (rmax == 0) return fp64 ? launch_voxel_t<double, 0>(L, st) : launch_voxel_t<float, 0>(L, st);
+    if (rmax == 1) return fp64 ? launch_voxel_t<double, 1>(L, st) : launch_voxel_t<float, 1>(L, st);
+    return fp64 ? launch_voxel_t<double, 2>(L, st) : launch_voxel_t<float, 2>(L, st);
 }
