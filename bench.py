@@ -74,7 +74,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -84,7 +84,15 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -96,7 +104,10 @@ class ClockSampler:
 
     def summary(self):
         sm, smax, reasons = [], [], set()
-        for ln in self.lines:
+        t0, t1 = getattr(self, "window", (-1e30, 1e30))
+        inside = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.05]
+        lines = inside if inside else [ln for (_, ln) in self.lines]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < len(self.FIELDS):
                 continue
@@ -112,7 +123,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": len(inside)}
 
 
 def cpu_oracle_rate(vol, target_s=12.0, threads=0, seed=0):
@@ -171,7 +182,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="spine", choices=["spine", "brain", "tiny"])
@@ -179,6 +190,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip form comparison and at-scale lines")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--no-fit", action="store_true", help="use the default variogram instead of the LOO fit")
+    ap.add_argument("--no-loo", action="store_true", help="skip the leave-one-slice-out fwd+bwd timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -209,6 +222,17 @@ def main():
     vol = workload(args.workload)
     s_host = torch.from_numpy(np.ascontiguousarray(vol.slices))
     s_dev = s_host.to(dev)
+    variogram_fit = None
+    if args.workload == "spine" and not args.no_fit:
+        # the spine configuration uses a spherical variogram fitted to the slice data: fit it by gradient
+        # descent on the leave-one-slice-out loss (CUDA kernels), before anything is timed
+        from paper_2303_09523_gb300 import fit
+        vals = torch.from_numpy(vol.values_f64().astype(np.float32)).to(dev)
+        res = fit.fit_variogram_loo(vals, vol.zfactor, vol.half_w, vol.n_sub_blocks, "spherical", vol.sill,
+                                    init_range=8.0, init_ratio=0.05, steps=50, lr=0.1)
+        vol.nugget, vol.sill, vol.range = res["theta"]
+        variogram_fit = {"method": "leave-one-slice-out loss, Adam 50 steps on log range and log nugget/sill",
+                         "loss_first": res["losses"][0], "loss_final": res["loss"]}
     code = binding.dtype_code(s_dev.dtype)
     desc = binding.desc_for(tuple(s_dev.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks, code, vol.in_scale)
     out_dt = binding.out_dtype(code)
@@ -231,7 +255,9 @@ def main():
     plan.get_timing()
     barrier()
     with ClockSampler(local) as clk:
+        clk.wait_first()
         t_wall = time.perf_counter()
+        t_start = t_wall
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
@@ -239,6 +265,7 @@ def main():
             ev[i][1].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
+        clk.mark(t_start, t_start + t_wall)
     plan.set_timing(False)
     kms, klaunch = plan.get_timing()
     plan.device_status(stream)
@@ -292,6 +319,10 @@ def main():
         peaks = {"fp32_fma_gflops": binding.measure_fma_peak(False), "fp64_fma_gflops": binding.measure_fma_peak(True)}
         extra = compare_forms(args, vol, s_dev, desc, params, out, dev, stream, peaks)
         extra["alu_peaks_measured"] = peaks
+    if rank == 0 and not args.no_loo:
+        extra["fwd_bwd"] = time_loo(args, vol, s_dev, desc, params, dev, stream, flush)
+    if variogram_fit is not None:
+        extra["variogram_fit"] = variogram_fit
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -323,6 +354,41 @@ def main():
     plan.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
+    """Leave-one-slice-out forward + backward (gradients w.r.t. every slice voxel and the variogram)."""
+    import torch
+    from paper_2303_09523_gb300 import binding
+    plan = binding.Plan([desc], form="DS", flags=binding.FLAG_LOO, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gl = torch.ones(1, dtype=torch.float64, device=dev)
+    gs = torch.empty(s_dev.shape, dtype=torch.float32, device=dev)
+    gp = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def step():
+        plan.loo_forward([s_dev], params, loss, None, stream)
+        plan.backward([s_dev], params, gl, [gs], gp, False, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    plan.device_status(stream)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    plan.close()
+    nvox = (vol.n - 2) * vol.H * vol.W
+    return {"value": nvox / (ms * 1e-3), "unit": "LOO-predicted voxels/s (forward + backward)", "ms_per_step": ms,
+            "voxels_per_step": nvox, "loss": float(loss.item()),
+            "grad_theta": [float(x) for x in gp.cpu()]}
 
 
 def p64_flops_per_voxel(vol):

@@ -110,6 +110,9 @@ typedef struct {
  *   device status becomes KRIG_ETIMEOUT (exercises failure detection without a
  *   real fault; the outputs of that call are not valid). */
 #define KRIG_FLAG_FAULT_TIMEOUT 0x100u
+/*   KRIG_FLAG_LOO: also size the workspace for krig_loo_forward / krig_backward
+ *   (DS form only; every volume needs n_known >= 3). */
+#define KRIG_FLAG_LOO 0x2u
 
 #define KRIG_MAX_VOLUMES 64
 
@@ -141,6 +144,35 @@ krig_status krig_plan_set_workspace(krig_plan_t plan, void* d_workspace, size_t 
  * Errors: KRIG_EINVAL, KRIG_EWORKSPACE, KRIG_ECUDA (launch). */
 krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void* const* d_out,
                              float* const* d_var, const krig_variogram* d_params, void* stream);
+
+/* Leave-one-slice-out cross-validation loss, the differentiable objective for
+ * fitting the variogram (the paper fixes none).  Each interior known slice j
+ * (1 <= j <= n-2) is predicted at its own z by ordinary kriging from slices
+ * j-1 and j+1 (a gap of 2g, target in the middle; same window, truncation and
+ * variogram as krig_interpolate), and
+ *     L_v = 1/((n-2) H W) * sum_j sum_{x,y} (P_j(x,y) - S_j(x,y))^2.
+ * Needs a plan created with KRIG_FLAG_LOO.
+ *   d_slices, d_params: as krig_interpolate.
+ *   d_pred: nullable host array of nullable device pointers, (n-2) x H x W
+ *           float32 predictions.
+ *   d_loss: device, [n_vols] float64 (overwritten).
+ * Errors: KRIG_EINVAL, KRIG_EUNSUPPORTED (plan without the flag), KRIG_EWORKSPACE,
+ * KRIG_ECUDA. */
+krig_status krig_loo_forward(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params,
+                             float* const* d_pred, double* d_loss, void* stream);
+
+/* Gradient of the LOO loss, scaled by the upstream gradient d_grad_loss[v]
+ * (device float64 per volume), with respect to
+ *   - every known-slice intensity (d_grad_slices: nullable host array of
+ *     nullable device pointers, n x H x W float32), and
+ *   - the variogram parameters (d_grad_params: nullable device float64
+ *     [n_vols][3] = d/d(nugget, sill, range)).
+ * With accumulate != 0 the gradients are added to the buffers; otherwise they
+ * are overwritten.  The class systems are solved again rather than stored.
+ * Errors: as krig_loo_forward. */
+krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params,
+                          const double* d_grad_loss, float* const* d_grad_slices, double* d_grad_params,
+                          int32_t accumulate, void* stream);
 
 /* Wait for the stream, then return and clear the plan's device error bits:
  * KRIG_OK, KRIG_ESINGULAR or KRIG_ETIMEOUT (the first set, in that order). */

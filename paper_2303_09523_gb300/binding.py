@@ -20,6 +20,8 @@ FORM_P64, FORM_PMX, FORM_DS = 0, 1, 2
 FORMS = {"P64": FORM_P64, "PMX": FORM_PMX, "DS": FORM_DS}
 MODELS = {"spherical": SPHERICAL, "exponential": EXPONENTIAL}
 FLAG_DS_FP64_SOLVE = 0x1
+FLAG_LOO = 0x2
+FLAG_FAULT_TIMEOUT = 0x100
 MAX_VOLUMES = 64
 TIMING_KINDS = 4
 
@@ -67,6 +69,10 @@ def lib(build_if_missing: bool = False):
     L.krig_plan_set_workspace.restype = ctypes.c_int
     L.krig_interpolate.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
     L.krig_interpolate.restype = ctypes.c_int
+    L.krig_loo_forward.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), vp, vp]
+    L.krig_loo_forward.restype = ctypes.c_int
+    L.krig_backward.argtypes = [vp, ctypes.POINTER(vp), vp, vp, ctypes.POINTER(vp), vp, ctypes.c_int32, vp]
+    L.krig_backward.restype = ctypes.c_int
     L.krig_plan_device_status.argtypes = [vp, vp]
     L.krig_plan_device_status.restype = ctypes.c_int
     L.krig_plan_set_timing.argtypes = [vp, ctypes.c_int32]
@@ -158,6 +164,25 @@ class Plan:
             V = (ctypes.c_void_p * n)(*[(0 if t is None else t.data_ptr()) for t in variances])
         _check(self._lib.krig_interpolate(self.handle, S, O, V, _ptr(params), _stream(stream)))
 
+    def loo_forward(self, slices, params, loss, preds=None, stream=None):
+        """Leave-one-slice-out loss per volume into ``loss`` (device float64 [n_vols])."""
+        n = len(self.descs)
+        S = (ctypes.c_void_p * n)(*[t.data_ptr() for t in slices])
+        Pp = None
+        if preds is not None:
+            Pp = (ctypes.c_void_p * n)(*[(0 if t is None else t.data_ptr()) for t in preds])
+        _check(self._lib.krig_loo_forward(self.handle, S, _ptr(params), Pp, _ptr(loss), _stream(stream)))
+
+    def backward(self, slices, params, grad_loss, grad_slices=None, grad_params=None, accumulate=False, stream=None):
+        """Gradients of the LOO loss (times grad_loss) w.r.t. slices and (nugget, sill, range)."""
+        n = len(self.descs)
+        S = (ctypes.c_void_p * n)(*[t.data_ptr() for t in slices])
+        G = None
+        if grad_slices is not None:
+            G = (ctypes.c_void_p * n)(*[(0 if t is None else t.data_ptr()) for t in grad_slices])
+        _check(self._lib.krig_backward(self.handle, S, _ptr(params), _ptr(grad_loss), G, _ptr(grad_params),
+                                       1 if accumulate else 0, _stream(stream)))
+
     def device_status(self, stream=None):
         _check(self._lib.krig_plan_device_status(self.handle, _stream(stream)))
 
@@ -225,3 +250,76 @@ def krige(volumes, form="DS", want_var=False, flags=0, stream=None):
     plan.device_status(stream)
     plan.close()
     return outs, vars_
+
+
+def variogram_from_theta(theta, model, device=None):
+    """Device krig_variogram buffer (uint8, 32 bytes) from a float64 tensor (nugget, sill, range).
+
+    Argument marshalling with tensor views only: the int32 model code and the
+    three doubles are written into one 4-double buffer.
+    """
+    import torch
+    code = MODELS[model] if isinstance(model, str) else int(model)
+    buf = torch.zeros(4, dtype=torch.float64, device=device if device is not None else theta.device)
+    buf[1:4] = theta.detach().to(torch.float64)
+    buf.view(torch.int32)[0] = code
+    return buf.view(torch.uint8)
+
+
+_loo_plans = {}
+
+
+def _loo_plan(shape, dtype_code_, zfactor, half_w, n_sub_blocks, in_scale, device):
+    key = (tuple(shape), dtype_code_, zfactor, half_w, n_sub_blocks, float(in_scale), str(device))
+    p = _loo_plans.get(key)
+    if p is None:
+        d = desc_for(tuple(shape), zfactor, half_w, n_sub_blocks, dtype_code_, in_scale)
+        p = Plan([d], form="DS", flags=FLAG_LOO, device=device)
+        _loo_plans[key] = p
+    return p
+
+
+def _make_loo_function():
+    import torch
+
+    class KrigLOO(torch.autograd.Function):
+        """Leave-one-slice-out MSE of the kriging interpolator, differentiable w.r.t. the slices
+        (float32 / float64 tensors) and theta = (nugget, sill, range) (float64 tensor)."""
+
+        @staticmethod
+        def forward(ctx, slices, theta, zfactor, half_w, n_sub_blocks, model):
+            code = dtype_code(slices.dtype)
+            s = slices.contiguous()
+            plan = _loo_plan(s.shape, code, zfactor, half_w, n_sub_blocks, 1.0, s.device)
+            params = variogram_from_theta(theta, model, s.device)
+            loss = torch.empty(1, dtype=torch.float64, device=s.device)
+            plan.loo_forward([s], params, loss)
+            ctx.save_for_backward(s, params)
+            ctx.plan = plan
+            ctx.slices_dtype = slices.dtype
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            s, params = ctx.saved_tensors
+            plan = ctx.plan
+            gl = grad_out.detach().to(torch.float64).reshape(1).contiguous()
+            gs = torch.empty(s.shape, dtype=torch.float32, device=s.device) if ctx.needs_input_grad[0] else None
+            gp = torch.empty(3, dtype=torch.float64, device=s.device) if ctx.needs_input_grad[1] else None
+            plan.backward([s], params, gl, [gs] if gs is not None else None, gp)
+            if gs is not None:
+                gs = gs.to(ctx.slices_dtype)
+            return gs, gp, None, None, None, None
+
+    return KrigLOO
+
+
+_KrigLOO = None
+
+
+def loo_loss(slices, theta, zfactor, half_w, n_sub_blocks=1, model="spherical"):
+    """Differentiable leave-one-slice-out loss (torch.autograd)."""
+    global _KrigLOO
+    if _KrigLOO is None:
+        _KrigLOO = _make_loo_function()
+    return _KrigLOO.apply(slices, theta, zfactor, half_w, n_sub_blocks, model)

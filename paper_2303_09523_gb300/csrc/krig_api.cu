@@ -51,6 +51,8 @@ struct Timing {
 
 }  // namespace
 
+static_assert(sizeof(KrigLaunch) <= 32000, "kernel parameter block exceeds the 32 KB parameter limit");
+
 struct krig_plan_s {
     std::vector<krig_volume_desc> desc;
     KrigLaunch L;
@@ -128,12 +130,16 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         return fail(KRIG_EINVAL, "n_vols must be in [1, %d] (got %d)", KRIG_MAX_VOLUMES, n_vols);
     if (form != KRIG_FORM_P64 && form != KRIG_FORM_PMX && form != KRIG_FORM_DS)
         return fail(KRIG_EINVAL, "unknown form %d", (int)form);
-    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT;
+    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT | KRIG_FLAG_LOO;
     if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
     for (int i = 0; i < n_vols; ++i) {
         krig_status st = check_desc(vols[i], i);
         if (st != KRIG_OK) return st;
+        if ((flags & KRIG_FLAG_LOO) && vols[i].n_known < 3)
+            return fail(KRIG_EINVAL, "volume %d: leave-one-slice-out needs n_known >= 3", i);
     }
+    if ((flags & KRIG_FLAG_LOO) && form != KRIG_FORM_DS)
+        return fail(KRIG_EUNSUPPORTED, "KRIG_FLAG_LOO needs the DS form");
     krig_plan_s* p = new (std::nothrow) krig_plan_s();
     if (!p) return fail(KRIG_ENOMEM, "out of host memory");
     p->desc.assign(vols, vols + n_vols);
@@ -150,6 +156,13 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
     for (int i = 0; i < n_vols; ++i)
         krig_fill_vol(L.vol[i], vols[i], form, chunk, &off, &items, &classes, &vox, &frames);
     L.n_frame_units = frames;
+    if (flags & KRIG_FLAG_LOO) {
+        int64_t lc = 0, li = 0, la = 0;
+        for (int i = 0; i < n_vols; ++i) krig_fill_loo(L.vol[i], &off, &lc, &li, &la);
+        L.n_loo_classes = lc;
+        L.n_loo_items = li;
+        L.n_loo_adj = la;
+    }
     L.n_items = items;
     L.n_classes = classes;
     L.n_vox = vox;
@@ -208,6 +221,66 @@ krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void
         if (s != KRIG_OK) return s;
     }
     return KRIG_OK;
+}
+
+static krig_status loo_common(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (!(plan->flags & KRIG_FLAG_LOO)) return fail(KRIG_EUNSUPPORTED, "plan was created without KRIG_FLAG_LOO");
+    if (!plan->ws) return fail(KRIG_EWORKSPACE, "no workspace set (krig_plan_set_workspace)");
+    if (!d_slices || !d_params) return fail(KRIG_EINVAL, "d_slices / d_params is NULL");
+    KrigLaunch& L = plan->L;
+    for (int v = 0; v < L.n_vols; ++v) {
+        if (!d_slices[v]) return fail(KRIG_EINVAL, "volume %d: null slice pointer", v);
+        if ((uintptr_t)d_slices[v] % 16) return fail(KRIG_EINVAL, "volume %d: slices must be 16-byte aligned", v);
+        L.in[v] = d_slices[v];
+        L.pred[v] = nullptr;
+        L.grad_slices[v] = nullptr;
+    }
+    L.vg = d_params;
+    return KRIG_OK;
+}
+
+krig_status krig_loo_forward(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params,
+                             float* const* d_pred, double* d_loss, void* stream)
+{
+    krig_status s = loo_common(plan, d_slices, d_params);
+    if (s != KRIG_OK) return s;
+    if (!d_loss) return fail(KRIG_EINVAL, "d_loss is NULL");
+    KrigLaunch& L = plan->L;
+    for (int v = 0; v < L.n_vols; ++v) L.pred[v] = d_pred ? d_pred[v] : nullptr;
+    L.loss = d_loss;
+    L.grad_loss = nullptr;
+    L.grad_params = nullptr;
+    L.accumulate = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    return timed_launch(plan, st, 2, [&] { return krig_launch_loo(L, 0, 0, 0, st); }, "loo forward launch");
+}
+
+krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params,
+                          const double* d_grad_loss, float* const* d_grad_slices, double* d_grad_params,
+                          int32_t accumulate, void* stream)
+{
+    krig_status s = loo_common(plan, d_slices, d_params);
+    if (s != KRIG_OK) return s;
+    if (!d_grad_loss) return fail(KRIG_EINVAL, "d_grad_loss is NULL");
+    KrigLaunch& L = plan->L;
+    int want_slices = 0;
+    for (int v = 0; v < L.n_vols; ++v) {
+        L.grad_slices[v] = d_grad_slices ? d_grad_slices[v] : nullptr;
+        want_slices |= L.grad_slices[v] != nullptr;
+    }
+    L.grad_loss = d_grad_loss;
+    L.grad_params = d_grad_params;
+    L.loss = nullptr;
+    L.accumulate = accumulate ? 1 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_grad_params && !accumulate) {
+        cudaError_t e = cudaMemsetAsync(d_grad_params, 0, sizeof(double) * 3 * L.n_vols, st);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing d_grad_params");
+    }
+    return timed_launch(plan, st, 3, [&] { return krig_launch_loo(L, 1, want_slices, d_grad_params != nullptr, st); },
+                        "backward launch");
 }
 
 krig_status krig_plan_device_status(krig_plan_t plan, void* stream)

@@ -48,6 +48,14 @@ struct KrigVol {
     int64_t frame_begin;      // first DS frame unit (32 frame pixels of one gap) of this volume
     int32_t frame_units;      // frame units per gap
     int32_t pad0;
+    // leave-one-slice-out (plans created with KRIG_FLAG_LOO)
+    int64_t loo_cls_begin;    // first LOO class block of this volume
+    int64_t loo_item_begin;   // first LOO residual tile (target slices 1..n-2)
+    int64_t loo_adj_begin;    // first LOO adjoint tile (slices 0..n-1)
+    int64_t lw_off;           // LOO weights [ncy][ncx][2][2r+1][2r+1] float
+    int64_t lbar_off;         // sum r S_k per class tap, same layout, double
+    int64_t res_off;          // residuals (n-2) x H x W float
+    int64_t lacc_off;         // loss accumulator, double
 };
 
 struct KrigLaunch {
@@ -65,13 +73,21 @@ struct KrigLaunch {
     int64_t n_vox;              // output voxels over all volumes
     int64_t n_frame_units;      // DS frame units over all volumes
     int32_t fault_timeout;      // test only: make one bounded device wait give up
-    int32_t pad0;
+    int32_t accumulate;         // LOO backward: add into grad_slices / grad_params
+    int64_t n_loo_classes, n_loo_items, n_loo_adj;
+    // per-call LOO arguments
+    float* pred[KRIG_MAX_VOLUMES];
+    float* grad_slices[KRIG_MAX_VOLUMES];
+    const double* grad_loss;    // [n_vols]
+    double* grad_params;        // [n_vols][3]
+    double* loss;               // [n_vols]
 };
 
 // Kernel launchers (krig_ds.cu, krig_voxel.cu). Return cudaError_t as int.
 int krig_launch_ds_solve(const KrigLaunch& L, int solve_fp64, void* stream);
 int krig_launch_ds_apply(const KrigLaunch& L, int grid, void* stream);
 int krig_launch_voxel(const KrigLaunch& L, int form, void* stream);
+int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int want_grad_params, void* stream);
 int krig_device_sm_count();
 
 // Set the thread-local message returned by krig_last_error() (krig_api.cu).
@@ -162,6 +178,29 @@ inline void krig_fill_vol(KrigVol& V, const krig_volume_desc& d, int form, int c
         *off = up(*off + krig_lag_bytes(V));
     }
     V.pad0 = 0;
+}
+
+// Leave-one-slice-out tables of one volume (plans with KRIG_FLAG_LOO).
+inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* items, int64_t* adj)
+{
+    const auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+    const int64_t taps = 2LL * (2 * V.r + 1) * (2 * V.r + 1);
+    const int64_t ncls = (int64_t)V.ncx * V.ncy;
+    const int64_t tiles = (int64_t)V.tiles_x * V.tiles_y;
+    V.loo_cls_begin = *classes;
+    *classes += ncls;
+    V.loo_item_begin = *items;
+    *items += (int64_t)(V.n - 2) * tiles;
+    V.loo_adj_begin = *adj;
+    *adj += (int64_t)V.n * tiles;
+    V.lw_off = *off;
+    *off = up(*off + ncls * taps * 4);
+    V.lbar_off = *off;
+    *off = up(*off + ncls * taps * 8);
+    V.res_off = *off;
+    *off = up(*off + (int64_t)(V.n - 2) * V.H * V.W * 4);
+    V.lacc_off = *off;
+    *off = up(*off + 8);
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times

@@ -1,0 +1,159 @@
+"""GPU leave-one-slice-out loss and adjoint against the FP64 oracle.
+
+Tolerances: loss and predictions within 1e-5 (relative / normwise), gradients
+w.r.t. the variogram parameters and the slice intensities within 1e-4 normwise
+(max |gpu - oracle| <= 1e-4 * max |oracle| per tensor).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2303_09523_gb300 import binding, phantoms
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(vol, theta, dtype=None, want=True):
+    t = torch.from_numpy(np.ascontiguousarray(vol.slices)).cuda()
+    if dtype is not None and t.dtype != torch.uint16:
+        t = t.to(dtype)
+    code = binding.dtype_code(t.dtype)
+    d = binding.desc_for(tuple(t.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks, code, vol.in_scale)
+    plan = binding.Plan([d], form="DS", flags=binding.FLAG_LOO)
+    params = binding.variogram_tensor([theta])
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    pred = torch.empty((vol.n - 2, vol.H, vol.W), dtype=torch.float32, device="cuda")
+    plan.loo_forward([t], params, loss, [pred])
+    out = {"loss": float(loss.item()), "pred": pred.double().cpu().numpy()}
+    if want:
+        gl = torch.ones(1, dtype=torch.float64, device="cuda")
+        gs = torch.empty(t.shape, dtype=torch.float32, device="cuda")
+        gp = torch.empty(3, dtype=torch.float64, device="cuda")
+        plan.backward([t], params, gl, [gs], gp)
+        out["grad_slices"] = gs.double().cpu().numpy()
+        out["grad_theta"] = gp.cpu().numpy()
+    plan.device_status()
+    plan.close()
+    vals = t.double().cpu().numpy() if t.dtype != torch.uint16 else vol.values_f64()
+    return out, vals
+
+
+def _nw(a, b):
+    """Normwise error; a reference that is exactly zero (e.g. the symmetric 2-point LOO weights do
+    not depend on theta at all) is compared absolutely."""
+    scale = np.abs(b).max()
+    return float(np.abs(a - b).max() / scale) if scale > 1e-12 else float(np.abs(a - b).max() * 1e8)
+
+
+CASES = [
+    ("spherical", 1, None),
+    ("exponential", 2, None),
+    ("spherical", 1, torch.float64),
+    ("exponential", 0, None),
+]
+
+
+@pytest.mark.parametrize("model,r,dtype", CASES)
+def test_loo_matches_oracle(model, r, dtype):
+    vol = phantoms.random_stack(6, 37, 45, 3, r, k=2, seed=50, model=model)
+    theta = dict(model=model, nugget=0.02, sill=vol.sill, range=6.0)
+    got, vals = _run(vol, theta, dtype)
+    ref = oracle.loo(vals, vol.zfactor, r, want_pred=True, want_grad_theta=True, want_grad_slices=True, **theta)
+    assert got["loss"] == pytest.approx(ref["loss"], rel=1e-5)
+    assert _nw(got["pred"], ref["pred"]) <= 1e-5
+    assert _nw(got["grad_theta"], ref["grad_theta"]) <= 1e-4
+    assert _nw(got["grad_slices"], ref["grad_slices"]) <= 1e-4
+
+
+def test_loo_uint16_spine_small():
+    vol = phantoms.spine(n=7, H=40, W=64, g=4, k=2)
+    theta = dict(model="spherical", nugget=0.0, sill=vol.sill, range=8.0)
+    got, vals = _run(vol, theta)
+    ref = oracle.loo(vals, vol.zfactor, vol.half_w, want_grad_theta=True, want_grad_slices=True, **theta)
+    assert got["loss"] == pytest.approx(ref["loss"], rel=1e-5)
+    assert _nw(got["grad_slices"], ref["grad_slices"]) <= 1e-4
+    # at zero nugget the weights do not depend on the sill, so dL/dsill = 0
+    assert abs(got["grad_theta"][1]) <= 1e-6 * np.abs(got["grad_theta"]).max()
+    assert _nw(got["grad_theta"][[0, 2]], ref["grad_theta"][[0, 2]]) <= 1e-4
+
+
+def test_loo_homogeneity_and_fd():
+    """nugget dL/dnugget + sill dL/dsill = 0; central differences (h = 1e-3) of the GPU loss in theta.
+
+    The GPU loss forms residuals in FP32, so its central difference carries about 1 % noise at this
+    step; the tight check is against the FP64 oracle gradient (itself pinned by central differences).
+    """
+    vol = phantoms.random_stack(5, 32, 40, 2, 1, k=1, seed=51)
+    theta = dict(model="spherical", nugget=0.05, sill=0.8, range=5.0)
+    got, vals = _run(vol, theta, torch.float64)
+    g = got["grad_theta"]
+    assert abs(theta["nugget"] * g[0] + theta["sill"] * g[1]) <= 1e-4 * np.abs(g).max()
+    ref = oracle.loo(vals, vol.zfactor, vol.half_w, want_grad_theta=True, **theta)
+    assert _nw(g, ref["grad_theta"]) <= 1e-4
+    for p, key in ((0, "nugget"), (2, "range")):
+        h = 1e-3
+        hi = dict(theta); hi[key] += h
+        lo = dict(theta); lo[key] -= h
+        fd = (_run(vol, hi, torch.float64, want=False)[0]["loss"] - _run(vol, lo, torch.float64, want=False)[0]["loss"]) / (2 * h)
+        assert g[p] == pytest.approx(fd, rel=2e-2, abs=1e-9)
+
+
+def test_backward_accumulate():
+    vol = phantoms.random_stack(5, 20, 24, 3, 1, k=1, seed=52)
+    t = torch.from_numpy(np.ascontiguousarray(vol.slices)).cuda()
+    d = binding.desc_for(tuple(t.shape), 3, 1, 1, binding.F32)
+    plan = binding.Plan([d], form="DS", flags=binding.FLAG_LOO)
+    params = binding.variogram_tensor([dict(model="spherical", nugget=0.01, sill=0.5, range=4.0)])
+    gl = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+    gs = torch.zeros(t.shape, dtype=torch.float32, device="cuda")
+    gp = torch.zeros(3, dtype=torch.float64, device="cuda")
+    plan.backward([t], params, gl, [gs], gp)
+    gs1, gp1 = gs.clone(), gp.clone()
+    plan.backward([t], params, gl, [gs], gp, accumulate=True)
+    assert torch.allclose(gs, 2 * gs1, rtol=1e-6, atol=0)
+    assert torch.allclose(gp, 2 * gp1, rtol=1e-6, atol=0)
+    plan.close()
+
+
+def test_autograd_function_matches_oracle():
+    vol = phantoms.random_stack(6, 30, 34, 2, 1, k=2, seed=53)
+    s = torch.from_numpy(vol.slices.astype(np.float32)).cuda().requires_grad_(True)
+    theta = torch.tensor([0.03, 0.7, 5.5], dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = binding.loo_loss(s, theta, 2, 1, 2, "exponential")
+    loss.backward()
+    ref = oracle.loo(vol.slices.astype(np.float64), 2, 1, want_grad_theta=True, want_grad_slices=True,
+                     model="exponential", nugget=0.03, sill=0.7, range=5.5)
+    assert float(loss.detach()) == pytest.approx(ref["loss"], rel=1e-5)
+    assert _nw(theta.grad.cpu().numpy(), ref["grad_theta"]) <= 1e-4
+    assert _nw(s.grad.double().cpu().numpy(), ref["grad_slices"]) <= 1e-4
+
+
+def test_fit_reaches_grid_minimum():
+    """50 Adam steps on log-range and the nugget/sill ratio (sill fixed: weights are 0-homogeneous in
+    (nugget, sill)) reach a loss within 1 % of the best of a brute-force grid."""
+    vol = phantoms.spine(n=10, H=64, W=64, g=4, k=3)
+    s = torch.from_numpy(vol.values_f64().astype(np.float32)).cuda()
+    sill = vol.sill
+    from paper_2303_09523_gb300 import fit
+    res = fit.fit_variogram_loo(s, vol.zfactor, vol.half_w, vol.n_sub_blocks, "spherical", sill,
+                                init_range=3.0, init_ratio=0.1, steps=50, lr=0.1)
+    losses = res["losses"]
+    assert losses[-1] < losses[0]
+    best = np.inf
+    for a in np.linspace(1.5, 30.0, 40):
+        for ratio in (0.0, 0.01, 0.03, 0.1, 0.3):
+            th = torch.tensor([ratio * sill, sill, a], dtype=torch.float64, device="cuda")
+            best = min(best, float(binding.loo_loss(s, th, vol.zfactor, vol.half_w, vol.n_sub_blocks, "spherical")))
+    assert res["loss"] <= best * 1.01
+
+
+def test_loo_full_size_spine():
+    """24 known 256x256 uint16 slices, g 4, 18 points: loss and gradients against the oracle."""
+    vol = phantoms.spine()
+    theta = dict(model="spherical", nugget=0.005, sill=vol.sill, range=8.0)
+    got, vals = _run(vol, theta)
+    ref = oracle.loo(vals, vol.zfactor, vol.half_w, want_grad_theta=True, want_grad_slices=True, **theta)
+    assert got["loss"] == pytest.approx(ref["loss"], rel=1e-5)
+    assert _nw(got["grad_theta"], ref["grad_theta"]) <= 1e-4
+    assert _nw(got["grad_slices"], ref["grad_slices"]) <= 1e-4
