@@ -494,42 +494,44 @@ __device__ __forceinline__ void ds_frame_pixel(const KrigVol& V, int f, int* x, 
     }
 }
 
-template <typename TI, int GM1>
+// Branch-free: tap coordinates are clamped into the slice and truncated taps
+// carry zero weight in the class row, so all 2(2R+1)^2 loads are independent
+// and in flight together.
+template <typename TI, int R, int GM1>
 __device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, int f0, int lane)
 {
     typedef typename DsTypes<TI>::TC TC;
     typedef typename DsTypes<TI>::TO TO;
+    constexpr int N2R = 2 * R + 1, NTAP = 2 * N2R * N2R;
     const KrigVol& V = P.vol[v];
     const int f = f0 + lane;
     if (f >= V.n_frame) return;
     int x, y;
     ds_frame_pixel(V, f, &x, &y);
-    const int r = V.r, W = V.W, H = V.H, g = V.g;
-    const int n2r = 2 * r + 1;
+    const int W = V.W, H = V.H, g = V.g;
     const int64_t plane = (int64_t)H * W;
-    const int cy = V.ymap[krig_slot(y, H, r)], cx = V.xmap[krig_slot(x, W, r)];
-    const TC* wrow = (const TC*)(P.ws + V.wtab_off) + ((int64_t)cy * V.ncx + cx) * (2 * n2r * n2r) * KRIG_TSLOTS;
-    const TI* in = (const TI*)P.in[v];
+    const int cy = V.ymap[krig_slot(y, H, R)], cx = V.xmap[krig_slot(x, W, R)];
+    const TC* wrow = (const TC*)(P.ws + V.wtab_off) + ((int64_t)cy * V.ncx + cx) * NTAP * KRIG_TSLOTS;
+    const TI* in = (const TI*)P.in[v] + (size_t)j * plane;
+    TC z[NTAP];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                const int yy = min(max(y + dy, 0), H - 1), xx = min(max(x + dx, 0), W - 1);
+                z[(s * N2R + dy + R) * N2R + dx + R] = (TC)__ldg(in + (size_t)s * plane + (size_t)yy * W + xx);
+            }
     TC acc[GM1];
 #pragma unroll
     for (int t = 0; t < GM1; ++t) acc[t] = TC(0);
-    for (int s = 0; s < 2; ++s) {
-        const TI* sl = in + (size_t)(j + s) * plane;
-        for (int dy = -r; dy <= r; ++dy) {
-            const int yy = y + dy;
-            if (yy < 0 || yy >= H) continue;
-            for (int dx = -r; dx <= r; ++dx) {
-                const int xx = x + dx;
-                if (xx < 0 || xx >= W) continue;
-                TC w[8];
-                ldgw8(wrow + ((s * n2r + (dy + r)) * n2r + (dx + r)) * KRIG_TSLOTS, w);
-                TC z;
-                if constexpr (sizeof(TI) == 2) z = (TC)sl[(size_t)yy * W + xx];  // weights carry the u16 scale
-                else z = (TC)sl[(size_t)yy * W + xx];
 #pragma unroll
-                for (int t = 0; t < GM1; ++t) acc[t] = fma(w[t], z, acc[t]);
-            }
-        }
+    for (int k = 0; k < NTAP; ++k) {
+        TC w[8];
+        ldgw8(wrow + k * KRIG_TSLOTS, w);
+#pragma unroll
+        for (int t = 0; t < GM1; ++t) acc[t] = fma(w[t], z[k], acc[t]);
     }
     TO* out = (TO*)P.out[v];
     float* var = P.var[v];
@@ -542,17 +544,27 @@ __device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, in
     }
 }
 
+template <typename TI, int GM1>
+__device__ __forceinline__ void ds_frame_r(const KrigLaunch& P, int v, int j, int f0, int lane)
+{
+    switch (P.vol[v].r) {
+    case 0: ds_frame_unit<TI, 0, GM1>(P, v, j, f0, lane); break;
+    case 1: ds_frame_unit<TI, 1, GM1>(P, v, j, f0, lane); break;
+    default: ds_frame_unit<TI, 2, GM1>(P, v, j, f0, lane); break;
+    }
+}
+
 template <typename TI>
 __device__ __forceinline__ void ds_frame_dispatch(const KrigLaunch& P, int v, int j, int f0, int lane)
 {
     switch (P.vol[v].g) {
-    case 2: ds_frame_unit<TI, 1>(P, v, j, f0, lane); break;
-    case 3: ds_frame_unit<TI, 2>(P, v, j, f0, lane); break;
-    case 4: ds_frame_unit<TI, 3>(P, v, j, f0, lane); break;
-    case 5: ds_frame_unit<TI, 4>(P, v, j, f0, lane); break;
-    case 6: ds_frame_unit<TI, 5>(P, v, j, f0, lane); break;
-    case 7: ds_frame_unit<TI, 6>(P, v, j, f0, lane); break;
-    case 8: ds_frame_unit<TI, 7>(P, v, j, f0, lane); break;
+    case 2: ds_frame_r<TI, 1>(P, v, j, f0, lane); break;
+    case 3: ds_frame_r<TI, 2>(P, v, j, f0, lane); break;
+    case 4: ds_frame_r<TI, 3>(P, v, j, f0, lane); break;
+    case 5: ds_frame_r<TI, 4>(P, v, j, f0, lane); break;
+    case 6: ds_frame_r<TI, 5>(P, v, j, f0, lane); break;
+    case 7: ds_frame_r<TI, 6>(P, v, j, f0, lane); break;
+    case 8: ds_frame_r<TI, 7>(P, v, j, f0, lane); break;
     default: break;  // g = 1: nothing to interpolate
     }
 }
@@ -683,6 +695,10 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
         return;
     }
     // ---------------- consumer warps
+    // The class solve may still be running (programmatic dependent launch):
+    // wait for it to complete before the first read of the weight tables.
+    // The producer warp streams input slices only and does not wait.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (P.fault_timeout && blockIdx.x == 0 && warp == 0) {
         // test hook: wait on a barrier nothing completes; the bounded wait gives up
         if (!mbar_wait(sh.never, 0, 1u << 12) && lane == 0) {
@@ -737,6 +753,19 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, cudaStream_t st)
     const int sms = krig_device_sm_count();
     int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     if (grid > L.n_items) grid = L.n_items;
-    k_ds_apply<TI><<<(unsigned)grid, DS_BLOCK, smem, st>>>(L);
+    // programmatic dependent launch: this grid may start while the class
+    // solve before it on the stream is still running
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(DS_BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_ds_apply<TI>, L);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }

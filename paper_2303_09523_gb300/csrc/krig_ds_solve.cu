@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     __shared__ double phi[8], vout[8];
 
     const int tid = threadIdx.x;
+    // let the stencil kernel launch now; it waits for this grid before it reads the tables
+    asm volatile("griddepcontrol.launch_dependents;");
     const int64_t cls = blockIdx.x;
     const int v = krig_find_vol(P, cls, 1);
     const KrigVol& V = P.vol[v];
