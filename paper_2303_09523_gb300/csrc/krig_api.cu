@@ -63,6 +63,8 @@ struct krig_plan_s {
     int timing = 0;
     std::vector<Timing> pending;
     std::vector<cudaEvent_t> pool;
+    DsTma tma;                              // tensor maps of the last call's slice pointers
+    const void* tma_ptr[KRIG_TMA_VOLS] = {};
     double ms[KRIG_TIMING_KINDS] = {0, 0, 0, 0};
     int64_t launches[KRIG_TIMING_KINDS] = {0, 0, 0, 0};
 };
@@ -142,6 +144,7 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         return fail(KRIG_EUNSUPPORTED, "KRIG_FLAG_LOO needs the DS form");
     krig_plan_s* p = new (std::nothrow) krig_plan_s();
     if (!p) return fail(KRIG_ENOMEM, "out of host memory");
+    memset(&p->tma, 0, sizeof(p->tma));
     p->desc.assign(vols, vols + n_vols);
     p->form = form;
     p->flags = flags;
@@ -214,7 +217,13 @@ krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void
         const int fp64 = (plan->flags & KRIG_FLAG_DS_FP64_SOLVE) ? 1 : 0;
         krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_ds_solve(L, fp64, st); }, "class solve launch");
         if (s != KRIG_OK) return s;
-        s = timed_launch(plan, st, 1, [&] { return krig_launch_ds_apply(L, 0, st); }, "stencil launch");
+        for (int v = 0; v < L.n_vols && v < KRIG_TMA_VOLS; ++v) {
+            if (plan->tma_ptr[v] != L.in[v]) {
+                plan->tma.valid[v] = krig_encode_ds_tma(L.vol[v], L.in[v], &plan->tma.tm[v]) == 0 ? 1 : 0;
+                plan->tma_ptr[v] = L.in[v];
+            }
+        }
+        s = timed_launch(plan, st, 1, [&] { return krig_launch_ds_apply(L, plan->tma, st); }, "stencil launch");
         if (s != KRIG_OK) return s;
     } else {
         krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_voxel(L, plan->form, st); }, "voxel solve launch");

@@ -547,22 +547,34 @@ __device__ bool block_gj_solve(GJSmem& S, const LagDims& d, const double* gC, in
     if (tid == 0) S.flag = 1;
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
+    constexpr int RW = (KRIG_KMAX + NT / 32 - 1) / (NT / 32);  // rows per warp
     for (int k = 0; k < K; ++k) {
         const float piv = A[k * LDA + k];
         if (!(piv > 0.0f)) {  // uniform: every thread reads the same pivot
             if (tid == 0) S.flag = 0;
             break;
         }
-        const float ip = 1.0f / piv;
-        // rows over warps, the K columns that can still be nonzero over lanes:
-        // left k+1..K-1, right K..K+k
+        const float ip = __frcp_rn(piv);
+        // rows over warps, the K columns that can still be nonzero over lanes
+        // (left k+1..K-1, right K..K+k).  All operands are read before any
+        // write: within a step no element is both read and written.
         const int nl = K - 1 - k;
-        for (int i = warp; i < K; i += NT / 32) {
-            if (i == k) continue;
-            const float f = A[i * LDA + k] * ip;
-            for (int c = lane; c < K; c += 32) {
-                const int j = c < nl ? k + 1 + c : K + (c - nl);
-                A[i * LDA + j] = fmaf(-f, A[k * LDA + j], A[i * LDA + j]);
+        const int j0 = lane < nl ? k + 1 + lane : K + (lane - nl);
+        const int j1 = lane + 32 < nl ? k + 33 + lane : K + (lane + 32 - nl);
+        const bool c0 = lane < K, c1 = lane + 32 < K;
+        const float rk0 = c0 ? A[k * LDA + j0] : 0.0f, rk1 = c1 ? A[k * LDA + j1] : 0.0f;
+        float f[RW];
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int i = warp + q * (NT / 32);
+            f[q] = (i < K && i != k) ? A[i * LDA + k] * ip : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int i = warp + q * (NT / 32);
+            if (i < K && i != k) {
+                if (c0) A[i * LDA + j0] = fmaf(-f[q], rk0, A[i * LDA + j0]);
+                if (c1) A[i * LDA + j1] = fmaf(-f[q], rk1, A[i * LDA + j1]);
             }
         }
         __syncthreads();

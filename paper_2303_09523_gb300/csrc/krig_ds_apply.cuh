@@ -31,10 +31,17 @@ template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; stati
 // RP (elements per shared row) >= TX + 2 PAD; RP * sizeof is 64 mod 128 bytes so the
 // two rows read by a quarter warp fall in different banks.
 
-#define DS_STAGES 4
 #define DS_CONSUMERS 8  // consumer warps; one more warp produces
 #define DS_BLOCK ((DS_CONSUMERS + 1) * 32)
 #define DS_WAIT_LIMIT (1u << 22)
+
+// Ring depth per input type: enough slots that the producer runs many slices
+// ahead of the consumers (a DRAM round trip spans many short gaps), within
+// about 64-80 KB of shared memory per block so two blocks fit on an SM.
+template <typename TI> struct DsStages;
+template <> struct DsStages<uint16_t> { static constexpr int S = 16; };
+template <> struct DsStages<float> { static constexpr int S = 12; };
+template <> struct DsStages<double> { static constexpr int S = 6; };
 
 // ---------------------------------------------------------------------------
 // mbarrier and bulk-copy primitives (inline PTX)
@@ -84,6 +91,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
+}
+
+// 3-D tiled TMA load of one box into shared memory; completion on the mbarrier.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -573,6 +590,7 @@ template <typename TI, int R, int GM1>
 __device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
                                              const DsShared& sh, int warp, int lane)
 {
+    constexpr int DS_STAGES = DsStages<TI>::S;
     const KrigVol& V = P.vol[d.v];
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
@@ -616,8 +634,19 @@ __device__ __forceinline__ void ds_consume_g(const KrigLaunch& P, const DsItem& 
 
 template <typename TI>
 __device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in, const DsItem& d, int s, TI* slot,
-                                                 uint64_t* bar, int lane)
+                                                 uint64_t* bar, int lane, const CUtensorMap* map)
 {
+    if (map) {
+        // one tensor-map request per slice tile; rows and columns outside the
+        // stack arrive as zeros (they meet zero weights of truncated taps)
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(DsTypes<TI>::RP * (KRIG_TY + 2 * V.r) * sizeof(TI));
+            mbar_arrive_expect_tx(bar, bytes);
+            tma_load_3d(slot, map, d.x0 - DsTypes<TI>::PAD, d.y0 - V.r, s, bar);
+        }
+        __syncwarp();
+        return;
+    }
     const int64_t plane = (int64_t)V.H * V.W;
     const TI* src = in + (size_t)s * plane;
     const bool bulk = (V.W % (16 / (int)sizeof(TI))) == 0;
@@ -640,10 +669,12 @@ __device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in,
 // One kernel per input type (compiled in separate translation units); items
 // of volumes of another type are skipped.
 template <typename TI>
-__global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P)
+__global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P,
+                                                          const __grid_constant__ DsTma T)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int RP = DsTypes<TI>::RP;
+    constexpr int DS_STAGES = DsStages<TI>::S;
     constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * RP;  // slot stride, elements
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     TI* slots = (TI*)sm;
@@ -680,7 +711,8 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
                     break;
                 }
                 fence_proxy_async_smem();
-                ds_produce_slice<TI>(V, (const TI*)P.in[d.v], d, s, slots + slot * stride, &sh.full[slot], lane);
+                const CUtensorMap* map = (d.v < KRIG_TMA_VOLS && T.valid[d.v]) ? &T.tm[d.v] : nullptr;
+                ds_produce_slice<TI>(V, (const TI*)P.in[d.v], d, s, slots + slot * stride, &sh.full[slot], lane, map);
             }
         }
         if (!ok) {
@@ -706,20 +738,8 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
             atomicExch(sh.abort, 1);
         }
     }
-    int q = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        DsItem d;
-        if (!ds_decode(P, it, dtype, d)) continue;
-        if (*(volatile int*)sh.abort) break;
-        switch (P.vol[d.v].r) {
-        case 0: ds_consume_g<TI, 0>(P, d, q, slots, stride, sh, warp, lane); break;
-        case 1: ds_consume_g<TI, 1>(P, d, q, slots, stride, sh, warp, lane); break;
-        default: ds_consume_g<TI, 2>(P, d, q, slots, stride, sh, warp, lane); break;
-        }
-        q += d.c1 - d.c0 + 1;
-    }
-    // frame units, spread over every consumer warp of the grid
-    if (*(volatile int*)sh.abort) return;
+    // frame units first (latency-bound reads through L2, overlapping the
+    // producer's first fills), spread over every consumer warp of the grid
     const int64_t nfu = P.n_frame_units;
     for (int64_t u = (int64_t)blockIdx.x * DS_CONSUMERS + warp; u < nfu; u += (int64_t)gridDim.x * DS_CONSUMERS) {
         int v = 0;
@@ -732,16 +752,29 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
         const int f0 = (int)(lu % V.frame_units) * 32;
         ds_frame_dispatch<TI>(P, v, j, f0, lane);
     }
+    int q = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        DsItem d;
+        if (!ds_decode(P, it, dtype, d)) continue;
+        if (*(volatile int*)sh.abort) break;
+        switch (P.vol[d.v].r) {
+        case 0: ds_consume_g<TI, 0>(P, d, q, slots, stride, sh, warp, lane); break;
+        case 1: ds_consume_g<TI, 1>(P, d, q, slots, stride, sh, warp, lane); break;
+        default: ds_consume_g<TI, 2>(P, d, q, slots, stride, sh, warp, lane); break;
+        }
+        q += d.c1 - d.c0 + 1;
+    }
 }
 
 template <typename TI>
-int krig_launch_ds_apply_t(const KrigLaunch& L, cudaStream_t st)
+int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
 {
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     bool any = false;
     for (int v = 0; v < L.n_vols; ++v) any = any || L.vol[v].dtype == dtype;
     if (!any) return 0;
     constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;
+    constexpr int DS_STAGES = DsStages<TI>::S;
     const size_t smem = (size_t)DS_STAGES * stride * sizeof(TI) + (2 * DS_STAGES + 2) * sizeof(uint64_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ds_apply<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -765,7 +798,7 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, cudaStream_t st)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_ds_apply<TI>, L);
+    e = cudaLaunchKernelEx(&cfg, k_ds_apply<TI>, L, T);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 // Nothing here is part of the public ABI (include/krig.h is).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is reached through the runtime's entry-point query)
 #include <stdint.h>
 
 #include "../../include/krig.h"
@@ -83,9 +84,21 @@ struct KrigLaunch {
     double* loss;               // [n_vols]
 };
 
+// TMA tensor maps of the known-slice stacks for the DS stencil: one 3-D map
+// (x, y, slice) per volume, box = one tile row span x (tile rows + halo) x 1
+// slice, zeros outside the stack.  Volumes past KRIG_TMA_VOLS, or whose rows
+// are not a 16-byte multiple, use the row-copy path.
+#define KRIG_TMA_VOLS 16
+struct DsTma {
+    CUtensorMap tm[KRIG_TMA_VOLS];
+    int32_t valid[KRIG_TMA_VOLS];
+};
+// Encode the map of volume V at device address ptr; 0 on success.
+int krig_encode_ds_tma(const KrigVol& V, const void* ptr, CUtensorMap* out);
+
 // Kernel launchers (krig_ds.cu, krig_voxel.cu). Return cudaError_t as int.
 int krig_launch_ds_solve(const KrigLaunch& L, int solve_fp64, void* stream);
-int krig_launch_ds_apply(const KrigLaunch& L, int grid, void* stream);
+int krig_launch_ds_apply(const KrigLaunch& L, const DsTma& T, void* stream);
 int krig_launch_voxel(const KrigLaunch& L, int form, void* stream);
 int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int want_grad_params, void* stream);
 int krig_device_sm_count();

@@ -111,7 +111,10 @@ extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, co
     if (e != cudaSuccess) return noalloc_fail(KRIG_ECUDA, std::string("clearing the status word: ") + cudaGetErrorString(e));
     int err = krig_launch_ds_solve(L, 0, s);
     if (err) return noalloc_fail(KRIG_ECUDA, std::string("class solve launch: ") + cudaGetErrorString((cudaError_t)err));
-    err = krig_launch_ds_apply(L, 0, s);
+    DsTma tma;  // host-side encoding of the slice pointer, passed by value to the kernel
+    memset(&tma, 0, sizeof(tma));
+    tma.valid[0] = krig_encode_ds_tma(V, d_slices, &tma.tm[0]) == 0 ? 1 : 0;
+    err = krig_launch_ds_apply(L, tma, s);
     if (err) return noalloc_fail(KRIG_ECUDA, std::string("stencil launch: ") + cudaGetErrorString((cudaError_t)err));
     if (check_status) {
         uint32_t bits = 0;
