@@ -174,6 +174,16 @@ krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const k
                           const double* d_grad_loss, float* const* d_grad_slices, double* d_grad_params,
                           int32_t accumulate, void* stream);
 
+/* Autotune the DS schedule on the caller's data: time krig_interpolate (iters
+ * calls each, synchronously on `stream`) for several work-item lengths (gaps
+ * per item: 1, 2, 3, 4, 6, 8, 12, 16 and whole sub-blocks) and keep the
+ * fastest.  The choice changes only the schedule: every choice gives
+ * bit-identical results.  Writes to d_out.  Not capturable; call it before
+ * capturing a graph.  *chunk_out (nullable) receives the chosen length.
+ * Errors: as krig_interpolate; KRIG_EUNSUPPORTED for P64 / PMX plans. */
+krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, void* const* d_out,
+                               const krig_variogram* d_params, int32_t iters, void* stream, int32_t* chunk_out);
+
 /* Wait for the stream, then return and clear the plan's device error bits:
  * KRIG_OK, KRIG_ESINGULAR or KRIG_ETIMEOUT (the first set, in that order). */
 krig_status krig_plan_device_status(krig_plan_t plan, void* stream);

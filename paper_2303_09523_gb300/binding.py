@@ -73,6 +73,9 @@ def lib(build_if_missing: bool = False):
     L.krig_loo_forward.restype = ctypes.c_int
     L.krig_backward.argtypes = [vp, ctypes.POINTER(vp), vp, vp, ctypes.POINTER(vp), vp, ctypes.c_int32, vp]
     L.krig_backward.restype = ctypes.c_int
+    L.krig_plan_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_int32, vp,
+                                     ctypes.POINTER(ctypes.c_int32)]
+    L.krig_plan_autotune.restype = ctypes.c_int
     L.krig_plan_device_status.argtypes = [vp, vp]
     L.krig_plan_device_status.restype = ctypes.c_int
     L.krig_plan_set_timing.argtypes = [vp, ctypes.c_int32]
@@ -182,6 +185,33 @@ class Plan:
             G = (ctypes.c_void_p * n)(*[(0 if t is None else t.data_ptr()) for t in grad_slices])
         _check(self._lib.krig_backward(self.handle, S, _ptr(params), _ptr(grad_loss), G, _ptr(grad_params),
                                        1 if accumulate else 0, _stream(stream)))
+
+    def autotune(self, slices, outs, params, iters=5, stream=None):
+        """Pick the fastest work-item length on this data (bit-identical results); returns it."""
+        n = len(self.descs)
+        S = (ctypes.c_void_p * n)(*[t.data_ptr() for t in slices])
+        O = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+        c = ctypes.c_int32()
+        _check(self._lib.krig_plan_autotune(self.handle, S, O, _ptr(params), iters, _stream(stream), ctypes.byref(c)))
+        return c.value
+
+    def capture(self, slices, outs, params, variances=None, stream=None):
+        """Capture one interpolate call into a CUDA graph; returns the torch.cuda.CUDAGraph.
+
+        Replaying it re-runs the call on the same buffers; new variogram values
+        written into ``params`` (device memory) take effect at the next replay.
+        """
+        import torch
+        s = torch.cuda.Stream() if stream is None else stream
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.interpolate(slices, outs, params, variances, s)  # warm-up outside the capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.interpolate(slices, outs, params, variances, s)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
 
     def device_status(self, stream=None):
         _check(self._lib.krig_plan_device_status(self.handle, _stream(stream)))

@@ -292,6 +292,74 @@ krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const k
                         "backward launch");
 }
 
+// Re-cut every volume's sub-blocks into work items of `chunk` gaps (the
+// workspace layout does not depend on it).
+static void set_chunk(krig_plan_t plan, int chunk)
+{
+    KrigLaunch& L = plan->L;
+    int64_t items = 0;
+    for (int v = 0; v < L.n_vols; ++v) {
+        KrigVol& V = L.vol[v];
+        const int max_block = (V.n - 1 + V.k - 1) / V.k;
+        V.chunk = chunk < 1 ? 1 : (chunk > max_block ? max_block : chunk);
+        V.chunks = (max_block + V.chunk - 1) / V.chunk;
+        V.item_begin = items;
+        items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
+    }
+    L.n_items = items;
+}
+
+krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, void* const* d_out,
+                               const krig_variogram* d_params, int32_t iters, void* stream, int32_t* chunk_out)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (plan->form != KRIG_FORM_DS) return fail(KRIG_EUNSUPPORTED, "autotuning applies to the DS form");
+    if (iters < 1) iters = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    int max_block = 1;
+    for (int v = 0; v < plan->L.n_vols; ++v) {
+        const KrigVol& V = plan->L.vol[v];
+        max_block = std::max(max_block, (V.n - 1 + V.k - 1) / V.k);
+    }
+    const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 1 << 20};
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return fail(KRIG_ECUDA, "cudaEventCreate failed");
+    const int saved_timing = plan->timing;
+    plan->timing = 0;
+    int best = plan->L.vol[0].chunk, last = -1;
+    float best_ms = 1e30f;
+    krig_status s = KRIG_OK;
+    for (int c : cand) {
+        const int eff = std::min(c, max_block);
+        if (eff == last) continue;
+        last = eff;
+        set_chunk(plan, eff);
+        s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);  // warm-up
+        if (s != KRIG_OK) break;
+        cudaEventRecord(a, st);
+        for (int i = 0; i < iters && s == KRIG_OK; ++i) s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);
+        cudaEventRecord(b, st);
+        if (s != KRIG_OK) break;
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            s = fail(KRIG_ECUDA, "autotune timing failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = eff;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    plan->timing = saved_timing;
+    set_chunk(plan, best);
+    if (chunk_out) *chunk_out = best;
+    return s;
+}
+
 krig_status krig_plan_device_status(krig_plan_t plan, void* stream)
 {
     if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
