@@ -353,7 +353,7 @@ __device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
             TC w[8];
-            ldgw8(ow + (s * KRIG_NORB + o) * KRIG_TSLOTS, w);
+            ldw8(ow + (s * KRIG_NORB + o) * KRIG_TSLOTS, w);
 #pragma unroll
             for (int p = 0; p < KRIG_PX; ++p)
 #pragma unroll
@@ -400,6 +400,7 @@ __device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype
 }
 
 struct DsShared {
+    void* ow;          // interior orbit weights of volumes 0..KRIG_TMA_VOLS-1, [v][2][NORB][8]
     uint64_t* full;
     uint64_t* empty;
     uint64_t* never;  // test hook: a barrier nothing completes
@@ -412,7 +413,8 @@ struct DsShared {
 // border) are written by the frame units instead.
 template <typename TI, int R, int GM1>
 __device__ __forceinline__ void ds_gap(const KrigLaunch& P, const KrigVol& V, int v, const DsItem& d, int j,
-                                       const TI* lo, const TI* hi, int lrow, int lcol)
+                                       const TI* lo, const TI* hi, int lrow, int lcol,
+                                       const typename DsTypes<TI>::TC* ow)
 {
     typedef typename DsTypes<TI>::TC TC;
     typedef typename DsTypes<TI>::TO TO;
@@ -459,7 +461,7 @@ __device__ __forceinline__ void ds_gap(const KrigLaunch& P, const KrigVol& V, in
         for (int p = 0; p < KRIG_PX; ++p)
 #pragma unroll
             for (int t = 0; t < GM1; ++t) acc[p][t] = TC(0);
-        ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, (const TC*)(P.ws + V.otab_off));
+        ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, ow);
         const bool full = vec_out && plo == 0 && phi == KRIG_PX;
         const float vint = 0.0f;
         const float* vt = (const float*)(P.ws + V.vtab_off) + (int64_t)V.cint * KRIG_TSLOTS;
@@ -591,7 +593,11 @@ __device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& 
                                              const DsShared& sh, int warp, int lane)
 {
     constexpr int DS_STAGES = DsStages<TI>::S;
+    typedef typename DsTypes<TI>::TC TC;
     const KrigVol& V = P.vol[d.v];
+    // interior orbit weights: shared copy for the first volumes, global beyond
+    const TC* ow = d.v < KRIG_TMA_VOLS ? (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS)
+                                       : (const TC*)(P.ws + V.otab_off);
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int nsl = d.c1 - d.c0 + 1;
@@ -601,7 +607,7 @@ __device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& 
         ok = mbar_wait(&sh.full[qh % DS_STAGES], (qh / DS_STAGES) & 1, DS_WAIT_LIMIT);
         if (!ok) break;
         ds_gap<TI, R, GM1>(P, V, d.v, d, d.c0 + m, slots + (ql % DS_STAGES) * stride,
-                           slots + (qh % DS_STAGES) * stride, lrow, lcol);
+                           slots + (qh % DS_STAGES) * stride, lrow, lcol, ow);
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.empty[ql % DS_STAGES]);
     }
@@ -679,7 +685,9 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     TI* slots = (TI*)sm;
     uint64_t* bars = (uint64_t*)(sm + (size_t)DS_STAGES * stride * sizeof(TI));
-    DsShared sh{bars, bars + DS_STAGES, bars + 2 * DS_STAGES, (int*)(bars + 2 * DS_STAGES + 1)};
+    typedef typename DsTypes<TI>::TC TC;
+    TC* owsm = (TC*)(bars + 2 * DS_STAGES + 2);
+    DsShared sh{owsm, bars, bars + DS_STAGES, bars + 2 * DS_STAGES, (int*)(bars + 2 * DS_STAGES + 1)};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < DS_STAGES) {
         mbar_init(&sh.full[tid], 1);
@@ -731,6 +739,17 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     // wait for it to complete before the first read of the weight tables.
     // The producer warp streams input slices only and does not wait.
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the interior orbit weights, now final, into shared memory; a named
+    // barrier over the consumer warps only (the producer runs on)
+    {
+        const int nv = min(P.n_vols, KRIG_TMA_VOLS);
+        constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
+        for (int e = tid; e < nv * NW; e += DS_CONSUMERS * 32) {
+            const KrigVol& Vv = P.vol[e / NW];
+            owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(P.ws + Vv.otab_off))[e % NW] : TC(0);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
+    }
     if (P.fault_timeout && blockIdx.x == 0 && warp == 0) {
         // test hook: wait on a barrier nothing completes; the bounded wait gives up
         if (!mbar_wait(sh.never, 0, 1u << 12) && lane == 0) {
@@ -775,7 +794,9 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
     if (!any) return 0;
     constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;
     constexpr int DS_STAGES = DsStages<TI>::S;
-    const size_t smem = (size_t)DS_STAGES * stride * sizeof(TI) + (2 * DS_STAGES + 2) * sizeof(uint64_t);
+    typedef typename DsTypes<TI>::TC TC;
+    const size_t smem = (size_t)DS_STAGES * stride * sizeof(TI) + (2 * DS_STAGES + 2) * sizeof(uint64_t) +
+                        (size_t)KRIG_TMA_VOLS * 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(TC);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ds_apply<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
