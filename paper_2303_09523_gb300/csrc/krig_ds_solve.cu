@@ -123,10 +123,285 @@ __device__ __forceinline__ int ds_class_setup(const KrigVol& V, const LagDims& d
     return K;
 }
 
+// ---------------------------------------------------------------------------
+// Class solve by the Z-mirror split (FP32 factorisation, FP64 refinement).
+//
+// Both known slices carry the same in-plane window, so with the points
+// ordered (lower slice, upper slice) the covariance matrix is C = [A B; B A]:
+// A between points of one slice (dz = 0), B across the gap (dz = g), both
+// symmetric.  x = [x0; x1] solves C x = [b0; b1] iff s = x0 + x1 and
+// d = x0 - x1 solve (A + B) s = b0 + b1 and (A - B) d = b0 - b1, two SPD
+// systems of n = nx * ny points each (C is SPD and the map is orthogonal up
+// to a factor).  The ones vector gives b0 = b1 = 1 (d = 0); target t gives
+// b0 = c_t, b1 = c_{g-t} (covariances to the lower / upper slice), so the sum
+// system needs t = 1..floor(g/2) plus ones and the difference system
+// t = 1..floor((g-1)/2); the other targets are the same columns mirrored.
+// Ordinary kriging (Appendix A, one constant predictor) then gives
+// u = C^-1 c0, v = C^-1 1, phi = (1'u - 1) / (1'v), w = u - phi v and the
+// kriging variance C(0) - w'c0 - phi.
+// ---------------------------------------------------------------------------
+constexpr int ZN = (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1);  // in-plane points, <= 25
+constexpr int ZL = 32;                                         // register row: n + m <= 25 + 5
+static_assert(ZN + 1 + KRIG_GMAX / 2 <= ZL, "register row too short");
+static_assert(ZN * 8 <= 256, "one refinement entry per thread");
+// distinct lags: (a >= b) pairs in [0, 2r] for dz = 0 and g, in [0, r] for dz = 1..g-1
+constexpr int ZEV = (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 2) + (KRIG_GMAX - 1) * (KRIG_RMAX + 1) * (KRIG_RMAX + 2) / 2;
+
+struct ZSmem {
+    double T[2][ZN];          // A + B, A - B entries by in-plane lag ay * (2r+1) + ax
+    float Tf[2][ZN];
+    double B[2][ZN][8];       // right-hand sides
+    double X[2][ZN][8];       // solutions
+    float R[2][ZN][8];        // FP64 residuals rounded to FP32
+    float Ai[2][ZN][ZN + 1];  // FP32 inverses, padded rows
+    double W[2][ZN][8];       // weights: [slice][point][t-1]
+    double var[8];            // kriging variance per target
+    int8_t dx[ZL], dy[ZL];
+    int fail;
+};
+
 union DsSolveSmem {
     SolveSmem<double, KRIG_KMAX, 8> f64;
-    GJSmem gj;
+    ZSmem z;
 };
+
+// (a, b), a >= b >= 0, from its index a (a + 1) / 2 + b.
+__device__ __forceinline__ void ds_pair(int idx, int* a, int* b)
+{
+    int q = 0;
+    while ((q + 1) * (q + 2) / 2 <= idx) ++q;
+    *a = q;
+    *b = idx - q * (q + 1) / 2;
+}
+
+// Lag tables gC and g0 (same layout as krig_fill_lags) with one covariance
+// evaluation per distinct lag: the in-plane part of a lag depends only on
+// (max, min) of |dx|, |dy|, and the upper-slice target lags (dz = g - t)
+// repeat the lower-slice ones (dz = t).
+__device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* gC, double* g0, double* ev, int tid,
+                             int nt)
+{
+    const int nCp = d.n2r * (d.n2r + 1) / 2, n0p = d.nr * (d.nr + 1) / 2;
+    const int ne = 2 * nCp + (d.g - 1) * n0p;
+    for (int e = tid; e < ne; e += nt) {
+        int a, b;
+        double dz;
+        if (e < 2 * nCp) {
+            ds_pair(e % nCp, &a, &b);
+            dz = (double)((e / nCp) * d.g);
+        } else {
+            const int f = e - 2 * nCp;
+            ds_pair(f % n0p, &a, &b);
+            dz = (double)(f / n0p + 1);
+        }
+        ev[e] = krig_cov(v, (double)(a * a + b * b) + dz * dz);
+    }
+    __syncthreads();
+    const int nC = d.nC(), n0 = d.n0();
+    for (int e = tid; e < nC + n0; e += nt) {
+        if (e < nC) {
+            const int ax = e % d.n2r, ay = (e / d.n2r) % d.n2r, s = e / (d.n2r * d.n2r);
+            const int a = max(ax, ay), b = min(ax, ay);
+            gC[e] = ev[s * nCp + a * (a + 1) / 2 + b];
+        } else {
+            const int f = e - nC;
+            const int ax = f % d.nr, ay = (f / d.nr) % d.nr, s = (f / (d.nr * d.nr)) % 2, t = f / (2 * d.nr * d.nr) + 1;
+            const int a = max(ax, ay), b = min(ax, ay), dz = s == 0 ? t : d.g - t;
+            g0[f] = ev[2 * nCp + (dz - 1) * n0p + a * (a + 1) / 2 + b];
+        }
+    }
+    __syncthreads();
+}
+
+// Gauss-Jordan on [S | B] by one warp, lane i holding row i in registers.
+// Each step drops the pivot column from the front of every row and appends
+// the identity column it turns into, so that every register index is static:
+// after n steps a row holds [X | 0 | S^-1] (up to the row's pivot, divided out
+// at the end).  No pivoting (S is SPD); a pivot that is not positive fails.
+__device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, int n2r, float* X, float* Ai, int lane)
+{
+    float r[ZL];
+    const bool row = lane < n;
+    const int dxi = row ? S.dx[lane] : 0, dyi = row ? S.dy[lane] : 0;
+#pragma unroll
+    for (int j = 0; j < ZL; ++j) {
+        float a = 0.0f;
+        if (row) {
+            if (j < n) a = S.Tf[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])];
+            else if (j < n + m) a = (float)S.B[z][lane][j - n];
+        }
+        r[j] = a;
+    }
+    float dk = 1.0f;
+    bool ok = true;
+    for (int k = 0; k < n; ++k) {
+        const float p0 = __shfl_sync(0xffffffffu, r[0], k);
+        if (!(p0 > 0.0f)) {  // the same value in every lane
+            ok = false;
+            break;
+        }
+        const bool piv = lane == k;
+        const float fi = r[0] * __frcp_rn(p0);
+        const float f = piv ? 0.0f : fi;
+        if (piv) dk = p0;
+#pragma unroll
+        for (int j = 0; j + 1 < ZL; ++j) {
+            const float pj = __shfl_sync(0xffffffffu, r[j + 1], k);
+            r[j] = fmaf(-f, pj, r[j + 1]);
+        }
+        r[ZL - 1] = piv ? 1.0f : -fi;
+    }
+    if (ok && row) {
+        const float di = 1.0f / dk;
+#pragma unroll
+        for (int j = 0; j < ZL; ++j) {
+            if (j < m) X[lane * 8 + j] = r[j] * di;
+            if (j >= ZL - n) Ai[lane * (ZN + 1) + j - (ZL - n)] = r[j] * di;
+        }
+    }
+    return ok;
+}
+
+// Solve, combine and write one truncation class (FP32 factorisation).
+template <int NT>
+__device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, int cx, const LagDims& d,
+                                const double* gC, const double* g0, ZSmem& S, int tid)
+{
+    const int warp = tid >> 5, lane = tid & 31;
+    const int lx = V.xext[cx][0], rx = V.xext[cx][1], ly = V.yext[cy][0], ry = V.yext[cy][1];
+    const int nx = lx + rx + 1, ny = ly + ry + 1, n = nx * ny;
+    const int n2r = d.n2r, g = V.g, r = V.r;
+    const int hp = g / 2, hm = (g - 1) / 2;  // sum / difference targets
+    const int m0 = 1 + hp, m1 = hm;  // columns of the sum / difference system
+    // system entries by lag, points, right-hand sides
+    for (int e = tid; e < n2r * n2r; e += NT) {
+        const double a = gC[e], b = gC[n2r * n2r + e];
+        S.T[0][e] = a + b;
+        S.T[1][e] = a - b;
+        S.Tf[0][e] = (float)(a + b);
+        S.Tf[1][e] = (float)(a - b);
+    }
+    for (int e = tid; e < ZL; e += NT) {
+        S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
+        S.dy[e] = (int8_t)(e < n ? e / nx - ly : 0);
+    }
+    for (int e = tid; e < n * 8; e += NT) {
+        const int i = e >> 3, c = e & 7;
+        const int ax = abs(i % nx - lx), ay = abs(i / nx - ly);
+        double bp = 0.0, bm = 0.0;
+        if (c == 0) bp = 2.0;
+        else if (c <= hp) bp = g0[d.i0(c, 0, ay, ax)] + g0[d.i0(c, 1, ay, ax)];
+        if (c < hm) bm = g0[d.i0(c + 1, 0, ay, ax)] - g0[d.i0(c + 1, 1, ay, ax)];
+        S.B[0][i][c] = bp;
+        S.B[1][i][c] = bm;
+    }
+    if (tid == 0) S.fail = 0;
+    __syncthreads();
+    // FP32 factorisation: the sum system on warp 0, the difference system on warp 1
+    if (warp < 2 && (warp == 0 || m1 > 0)) {
+        const int z = warp;
+        if (!ds_warp_gj(S, z, n, z ? m1 : m0, n2r, &S.R[z][0][0], &S.Ai[z][0][0], lane) && lane == 0) S.fail = 1;
+    }
+    __syncthreads();
+    const bool ok = !S.fail;
+    // FP64 refinement: X = X32, R = B - S X in FP64, X += S^-1 R in FP32
+    const int nv = n * (m0 + m1);  // (system, point, column) triples
+    if (ok) {
+        for (int e = tid; e < nv; e += NT) {
+            const int z = e < n * m0 ? 0 : 1, f = z ? e - n * m0 : e, m = z ? m1 : m0;
+            S.X[z][f / m][f % m] = (double)S.R[z][f / m][f % m];
+        }
+        __syncthreads();
+        // one (system, point, column) per thread: nv <= ZN * 8 <= NT
+        const int z = tid < n * m0 ? 0 : 1, f = z ? tid - n * m0 : tid, m = z ? m1 : m0;
+        const int i = m ? f / m : 0, c = m ? f % m : 0;
+        float res = 0.0f;
+        if (tid < nv) {
+            const int dxi = S.dx[i], dyi = S.dy[i];
+            double acc = S.B[z][i][c];
+            for (int j = 0; j < n; ++j)
+                acc = fma(-S.T[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])], S.X[z][j][c], acc);
+            res = (float)acc;
+        }
+        __syncthreads();
+        if (tid < nv) S.R[z][i][c] = res;
+        __syncthreads();
+        if (tid < nv) {
+            float corr = 0.0f;
+            for (int j = 0; j < n; ++j) corr = fmaf(S.Ai[z][i][j], S.R[z][j][c], corr);
+            S.X[z][i][c] += (double)corr;
+        }
+        __syncthreads();
+        // combine, one warp per target t (lane = point):
+        //   sum column p = min(t, g-t), difference column p-1 with sign +1 for
+        //   t < g-t, -1 for t > g-t, none for t = g/2
+        if (warp < g - 1) {
+            const int t = warp + 1, p = min(t, g - t);
+            const bool in = lane < n;
+            const double sv = in ? S.X[0][lane][0] : 0.0, st = in ? S.X[0][lane][p] : 0.0;
+            double sd = 0.0;
+            if (in && t != g - t) sd = (t < g - t ? 1.0 : -1.0) * S.X[1][lane][p - 1];
+            double a = sv, b = st;
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            const double ph = (b - 1.0) / a;
+            const double w0 = 0.5 * (st + sd) - 0.5 * ph * sv, w1 = 0.5 * (st - sd) - 0.5 * ph * sv;
+            double wc = 0.0;
+            if (in) {
+                const int ax = abs(S.dx[lane]), ay = abs(S.dy[lane]);
+                wc = w0 * g0[d.i0(t, 0, ay, ax)] + w1 * g0[d.i0(t, 1, ay, ax)];
+                S.W[0][lane][t - 1] = w0;
+                S.W[1][lane][t - 1] = w1;
+            }
+            for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
+            if (lane == 0) S.var[t - 1] = gC[0] - wc - ph;
+        }
+        __syncthreads();
+    } else if (tid == 0) {
+        krig_set_status(P.status, KRIG_DEV_SINGULAR);
+    }
+    // weight-table row of the class: [s][dy+r][dx+r][t slot], zeros on
+    // truncated taps and unused t slots; u16 input: weights carry the scale
+    const int n2 = n2r * n2r, ntap = 2 * n2;
+    const double scale = V.dtype == KRIG_U16 ? (double)V.scale : 1.0;
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    const int64_t row = ((int64_t)cy * V.ncx + cx) * ntap * KRIG_TSLOTS;
+    for (int e = tid; e < ntap * KRIG_TSLOTS; e += NT) {
+        const int c = e % KRIG_TSLOTS, f = e / KRIG_TSLOTS;
+        const int dx = f % n2r - r, dy = (f / n2r) % n2r - r, s = f / n2;
+        double w = 0.0;
+        if (c < g - 1 && dx >= -lx && dx <= rx && dy >= -ly && dy <= ry)
+            w = ok ? S.W[s][(dy + ly) * nx + dx + lx][c] * scale : qnan;
+        if (V.dtype == KRIG_F64) ((double*)(P.ws + V.wtab_off))[row + e] = w;
+        else ((float*)(P.ws + V.wtab_off))[row + e] = (float)w;
+    }
+    // interior class: weights per D4 orbit (mean over the orbit's members)
+    if (cy * V.ncx + cx == V.cint) {
+        for (int e = tid; e < 2 * KRIG_NORB * KRIG_TSLOTS; e += NT) {
+            const int c = e % KRIG_TSLOTS, o = (e / KRIG_TSLOTS) % KRIG_NORB, s = e / (KRIG_TSLOTS * KRIG_NORB);
+            double sum = 0.0;
+            int cnt = 0;
+            if (c < g - 1) {
+                for (int dy = -r; dy <= r; ++dy)
+                    for (int dx = -r; dx <= r; ++dx) {
+                        const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy));
+                        if (a * (a + 1) / 2 + b != o) continue;
+                        sum += ok ? S.W[s][(dy + ly) * nx + dx + lx][c] : qnan;
+                        ++cnt;
+                    }
+            }
+            const double w = cnt ? sum / cnt * scale : 0.0;
+            if (V.dtype == KRIG_F64) ((double*)(P.ws + V.otab_off))[e] = w;
+            else ((float*)(P.ws + V.otab_off))[e] = (float)w;
+        }
+    }
+    if (tid < KRIG_TSLOTS) {
+        float* vt = (float*)(P.ws + V.vtab_off) + ((int64_t)cy * V.ncx + cx) * KRIG_TSLOTS;
+        vt[tid] = (tid < g - 1) ? (ok ? (float)S.var[tid] : __int_as_float(0x7fc00000)) : 0.0f;
+    }
+}
 
 template <typename TF>
 __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLaunch P)
@@ -135,6 +410,7 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     __shared__ double gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
     __shared__ double g0[(KRIG_GMAX - 1) * 2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
     __shared__ double phi[8], vout[8];
+    __shared__ double ev[ZEV];
 
     const int tid = threadIdx.x;
     // let the stencil kernel launch now; it waits for this grid before it reads the tables
@@ -148,8 +424,7 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     const krig_variogram vg = P.vg[v];
     const int r = V.r;
     LagDims d{r, V.g, 2 * r + 1, r + 1};
-    krig_fill_lags(d, vg, gC, g0, tid, 256);
-    __syncthreads();
+    ds_fill_lags(d, vg, gC, g0, ev, tid, 256);
     if (sizeof(TF) == 8) {
         SolveSmem<double, KRIG_KMAX, 8>& S = U.f64;
         const int K = ds_class_setup(V, d, g0, cy, cx, S.tap, S.Bd);
@@ -157,11 +432,7 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
         if (!ok && tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         ds_write_class(P, V, cy, cx, ok, S.Xd, S.Bd, S.tap, K, V.g, gC[0], phi, vout);
     } else {
-        GJSmem& S = U.gj;
-        const int K = ds_class_setup(V, d, g0, cy, cx, S.tap, S.Bd);
-        const bool ok = block_gj_solve<256>(S, d, gC, K, V.g, tid);
-        if (!ok && tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
-        ds_write_class(P, V, cy, cx, ok, S.Xd, S.Bd, S.tap, K, V.g, gC[0], phi, vout);
+        ds_class_zsplit<256>(P, V, cy, cx, d, gC, g0, U.z, tid);
     }
 }
 
