@@ -24,11 +24,13 @@ sys.path.insert(0, ROOT)
 METRIC = "kriged voxels/s on 1 GB300, mixed/batched vs plain FP64 at stated err; fwd+bwd vox/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
-# profiles/ (None until captured, and again whenever the kernel changes).
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel, from the ncu capture summarised in profiles/ (None until captured, and again
+# whenever the kernel changes).  Under ncu replay part of the output is still in L2 when
+# the launch ends, so these read below the algorithmic bytes.
 NCU_TRAFFIC = {
-    "spine": None,
-    "brain": None,
+    "spine": 3269888 + 111104,
+    "brain": 36651264 + 149990656,
 }
 
 
