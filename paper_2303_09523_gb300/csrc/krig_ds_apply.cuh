@@ -31,8 +31,10 @@ template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; stati
 // RP (elements per shared row) >= TX + 2 PAD; RP * sizeof is 64 mod 128 bytes so the
 // two rows read by a quarter warp fall in different banks.
 
-#define DS_CONSUMERS 8  // consumer warps; one more warp produces
-#define DS_BLOCK ((DS_CONSUMERS + 1) * 32)
+#define DS_CONSUMERS 8                      // consumer warps (tiles)
+#define DS_PRODUCER DS_CONSUMERS            // streams the known-slice tiles
+#define DS_FRAMER (DS_CONSUMERS + 1)        // border pixels (frame units)
+#define DS_BLOCK ((DS_CONSUMERS + 2) * 32)
 #define DS_WAIT_LIMIT (1u << 22)
 
 // Ring depth per input type: enough slots that the producer runs many slices
@@ -365,26 +367,41 @@ __device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc
 // ---------------------------------------------------------------------------
 // Persistent producer / consumer pipeline
 //
-// Blocks walk the work items round-robin.  Warp DS_CONSUMERS is the producer:
-// it streams every known slice the block needs, item after item, into a ring
-// of DS_STAGES slots ("full" barrier per slot, completed by the bulk copy),
-// after the consumers released the slot's previous slice ("empty" barrier,
-// one arrival per consumer warp).  The consumer warps compute gap after gap;
-// they never wait on each other.  Every wait is bounded; a wait that gives up
-// sets the device status KRIG_DEV_TIMEOUT and the shared abort flag, and the
-// producer then waits (bounded) for the copies it still has in flight.
+// Blocks walk the work items round-robin, shape by shape.  Warp DS_PRODUCER
+// streams every known slice the block needs, item after item, into a ring of
+// DS_STAGES slots ("full" barrier per slot, completed by the bulk copy), after
+// the consumers released the slot's previous slice ("empty" barrier, one
+// arrival per consumer warp).  The consumer warps compute gap after gap; they
+// never wait on each other.  Warp DS_FRAMER computes the border pixels beside
+// them.  Every wait is bounded; a wait that gives up sets the device status
+// KRIG_DEV_TIMEOUT and the shared abort flag, and the producer then waits
+// (bounded) for the copies it still has in flight.
 // ---------------------------------------------------------------------------
 struct DsItem {
     int v, x0, y0, c0, c1;
 };
 
-__device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype, DsItem& d)
+// Stencil shape of a volume: (r, g) as r * 8 + g - 1.  A block takes its
+// items shape by shape (ascending), round-robin within a shape, so that each
+// shape's loop runs in code compiled for that shape alone.
+#define DS_NSHAPE ((KRIG_RMAX + 1) * 8)
+__device__ __forceinline__ int ds_shape(const KrigVol& V) { return V.r * 8 + V.g - 1; }
+
+__device__ __forceinline__ uint32_t ds_shape_mask(const KrigLaunch& P, int dtype)
+{
+    uint32_t m = 0;
+    for (int v = 0; v < P.n_vols; ++v)
+        if (P.vol[v].dtype == dtype) m |= 1u << ds_shape(P.vol[v]);
+    return m;
+}
+
+__device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype, int shape, DsItem& d)
 {
     int v = 0;
     for (int u = 1; u < P.n_vols; ++u)
         if (P.vol[u].item_begin <= it) v = u;
     const KrigVol& V = P.vol[v];
-    if (V.dtype != dtype) return false;
+    if (V.dtype != dtype || ds_shape(V) != shape) return false;
     const int local = it - (int)V.item_begin;
     const int tiles = V.tiles_x * V.tiles_y;
     const int tile = local % tiles, rest = local / tiles;
@@ -405,6 +422,26 @@ struct DsShared {
     uint64_t* empty;
     uint64_t* never;  // test hook: a barrier nothing completes
     int* abort;
+};
+
+// Dynamic shared memory of k_ds_apply: DS_STAGES slots, the full and empty
+// barriers, the test barrier, the abort flag, the orbit weights.  Functions
+// derive the pointers from the base themselves (nothing goes through the
+// stack of a non-inlined call).
+extern __shared__ __align__(128) unsigned char ds_smem[];
+template <typename TI> struct DsLayout {
+    static constexpr int S = DsStages<TI>::S;
+    static constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;  // slot stride, elements
+    static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
+    static constexpr size_t bytes = bar_off + (2 * S + 2) * sizeof(uint64_t) +
+                                    (size_t)KRIG_TMA_VOLS * 2 * KRIG_NORB * KRIG_TSLOTS *
+                                        sizeof(typename DsTypes<TI>::TC);
+    __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
+    __device__ static __forceinline__ DsShared shared()
+    {
+        uint64_t* bars = (uint64_t*)(ds_smem + bar_off);
+        return DsShared{(void*)(bars + 2 * S + 2), bars, bars + S, bars + 2 * S, (int*)(bars + 2 * S + 1)};
+    }
 };
 
 // One gap of one item for the consumer warps: passthrough of known slice j
@@ -589,8 +626,8 @@ __device__ __forceinline__ void ds_frame_dispatch(const KrigLaunch& P, int v, in
 }
 
 template <typename TI, int R, int GM1>
-__device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
-                                             const DsShared& sh, int warp, int lane)
+__device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
+                                                const DsShared& sh, int warp, int lane)
 {
     constexpr int DS_STAGES = DsStages<TI>::S;
     typedef typename DsTypes<TI>::TC TC;
@@ -622,19 +659,36 @@ __device__ __noinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& 
     }
 }
 
-template <typename TI, int R>
-__device__ __forceinline__ void ds_consume_g(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
-                                             const DsShared& sh, int warp, int lane)
+// All items of one shape for this block, in its order; returns the slice
+// sequence number after them.  One non-inlined instance per shape, so the
+// call (and its register saves) happens once per block, not once per item.
+template <typename TI, int R, int GM1>
+__device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, int lane)
 {
-    switch (P.vol[d.v].g) {
-    case 1: ds_consume_item<TI, R, 0>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 2: ds_consume_item<TI, R, 1>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 3: ds_consume_item<TI, R, 2>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 4: ds_consume_item<TI, R, 3>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 5: ds_consume_item<TI, R, 4>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 6: ds_consume_item<TI, R, 5>(P, d, q, slots, stride, sh, warp, lane); break;
-    case 7: ds_consume_item<TI, R, 6>(P, d, q, slots, stride, sh, warp, lane); break;
-    default: ds_consume_item<TI, R, 7>(P, d, q, slots, stride, sh, warp, lane); break;
+    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    const DsShared sh = DsLayout<TI>::shared();
+    for (int it = blockIdx.x; it < (int)P.n_items; it += gridDim.x) {
+        DsItem d;
+        if (!ds_decode(P, it, dtype, R * 8 + GM1, d)) continue;
+        if (*(volatile int*)sh.abort) break;
+        ds_consume_item<TI, R, GM1>(P, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane);
+        q += d.c1 - d.c0 + 1;
+    }
+    return q;
+}
+
+template <typename TI, int R>
+__device__ __forceinline__ int ds_run_g(int g, const KrigLaunch& P, int q, int warp, int lane)
+{
+    switch (g) {
+    case 1: return ds_run_shape<TI, R, 0>(P, q, warp, lane);
+    case 2: return ds_run_shape<TI, R, 1>(P, q, warp, lane);
+    case 3: return ds_run_shape<TI, R, 2>(P, q, warp, lane);
+    case 4: return ds_run_shape<TI, R, 3>(P, q, warp, lane);
+    case 5: return ds_run_shape<TI, R, 4>(P, q, warp, lane);
+    case 6: return ds_run_shape<TI, R, 5>(P, q, warp, lane);
+    case 7: return ds_run_shape<TI, R, 6>(P, q, warp, lane);
+    default: return ds_run_shape<TI, R, 7>(P, q, warp, lane);
     }
 }
 
@@ -678,16 +732,13 @@ template <typename TI>
 __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P,
                                                           const __grid_constant__ DsTma T)
 {
-    extern __shared__ __align__(128) unsigned char sm[];
-    constexpr int RP = DsTypes<TI>::RP;
     constexpr int DS_STAGES = DsStages<TI>::S;
-    constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * RP;  // slot stride, elements
+    constexpr int stride = DsLayout<TI>::stride;
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
-    TI* slots = (TI*)sm;
-    uint64_t* bars = (uint64_t*)(sm + (size_t)DS_STAGES * stride * sizeof(TI));
+    TI* slots = DsLayout<TI>::slots();
     typedef typename DsTypes<TI>::TC TC;
-    TC* owsm = (TC*)(bars + 2 * DS_STAGES + 2);
-    DsShared sh{owsm, bars, bars + DS_STAGES, bars + 2 * DS_STAGES, (int*)(bars + 2 * DS_STAGES + 1)};
+    const DsShared sh = DsLayout<TI>::shared();
+    TC* owsm = (TC*)sh.ow;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < DS_STAGES) {
         mbar_init(&sh.full[tid], 1);
@@ -700,13 +751,19 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     fence_proxy_async_smem();
     __syncthreads();
     const int n_items = (int)P.n_items;
-    if (warp == DS_CONSUMERS) {
-        // ---------------- producer warp
+    const uint32_t shapes = ds_shape_mask(P, dtype);
+    if (warp == DS_PRODUCER) {
+        // ---------------- producer warp: the consumers' item order (shape by shape)
         int q = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (int it = blockIdx.x, c = 0; c < DS_NSHAPE && ok; it += gridDim.x) {
+            if (it >= n_items || !((shapes >> c) & 1u)) {
+                ++c;
+                it = (int)blockIdx.x - (int)gridDim.x;
+                continue;
+            }
             DsItem d;
-            if (!ds_decode(P, it, dtype, d)) continue;
+            if (!ds_decode(P, it, dtype, c, d)) continue;
             const KrigVol& V = P.vol[d.v];
             for (int s = d.c0; s <= d.c1; ++s, ++q) {
                 const int slot = q % DS_STAGES;
@@ -734,11 +791,29 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
         }
         return;
     }
-    // ---------------- consumer warps
     // The class solve may still be running (programmatic dependent launch):
     // wait for it to complete before the first read of the weight tables.
     // The producer warp streams input slices only and does not wait.
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (warp == DS_FRAMER) {
+        // ---------------- frame warp: border pixels (within r of the slice
+        // edge, their own truncation classes), latency-bound reads through L2,
+        // beside the consumers' tiles
+        const int64_t nfu = P.n_frame_units;
+        for (int64_t u = blockIdx.x; u < nfu; u += gridDim.x) {
+            int v = 0;
+            for (int w = 1; w < P.n_vols; ++w)
+                if (P.vol[w].frame_begin <= u) v = w;
+            const KrigVol& V = P.vol[v];
+            if (V.dtype != dtype || V.frame_units == 0) continue;
+            const int64_t lu = u - V.frame_begin;
+            const int j = (int)(lu / V.frame_units);
+            const int f0 = (int)(lu % V.frame_units) * 32;
+            ds_frame_dispatch<TI>(P, v, j, f0, lane);
+        }
+        return;
+    }
+    // ---------------- consumer warps
     // the interior orbit weights, now final, into shared memory; a named
     // barrier over the consumer warps only (the producer runs on)
     {
@@ -757,32 +832,15 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
             atomicExch(sh.abort, 1);
         }
     }
-    // frame units first (latency-bound reads through L2, overlapping the
-    // producer's first fills), spread over every consumer warp of the grid
-    const int64_t nfu = P.n_frame_units;
-    for (int64_t u = (int64_t)blockIdx.x * DS_CONSUMERS + warp; u < nfu; u += (int64_t)gridDim.x * DS_CONSUMERS) {
-        int v = 0;
-        for (int w = 1; w < P.n_vols; ++w)
-            if (P.vol[w].frame_begin <= u) v = w;
-        const KrigVol& V = P.vol[v];
-        if (V.dtype != dtype || V.frame_units == 0) continue;
-        const int64_t lu = u - V.frame_begin;
-        const int j = (int)(lu / V.frame_units);
-        const int f0 = (int)(lu % V.frame_units) * 32;
-        ds_frame_dispatch<TI>(P, v, j, f0, lane);
-    }
     int q = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        DsItem d;
-        if (!ds_decode(P, it, dtype, d)) continue;
-        if (*(volatile int*)sh.abort) break;
-        switch (P.vol[d.v].r) {
-        case 0: ds_consume_g<TI, 0>(P, d, q, slots, stride, sh, warp, lane); break;
-        case 1: ds_consume_g<TI, 1>(P, d, q, slots, stride, sh, warp, lane); break;
-        default: ds_consume_g<TI, 2>(P, d, q, slots, stride, sh, warp, lane); break;
-        }
-        q += d.c1 - d.c0 + 1;
+    for (int c = 0; c < DS_NSHAPE; ++c) {
+        if (!((shapes >> c) & 1u)) continue;
+        const int r = c / 8, g = c % 8 + 1;
+        if (r == 0) q = ds_run_g<TI, 0>(g, P, q, warp, lane);
+        else if (r == 1) q = ds_run_g<TI, 1>(g, P, q, warp, lane);
+        else q = ds_run_g<TI, 2>(g, P, q, warp, lane);
     }
+    (void)slots;
 }
 
 template <typename TI>
@@ -792,11 +850,7 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
     bool any = false;
     for (int v = 0; v < L.n_vols; ++v) any = any || L.vol[v].dtype == dtype;
     if (!any) return 0;
-    constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;
-    constexpr int DS_STAGES = DsStages<TI>::S;
-    typedef typename DsTypes<TI>::TC TC;
-    const size_t smem = (size_t)DS_STAGES * stride * sizeof(TI) + (2 * DS_STAGES + 2) * sizeof(uint64_t) +
-                        (size_t)KRIG_TMA_VOLS * 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(TC);
+    const size_t smem = DsLayout<TI>::bytes;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ds_apply<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;

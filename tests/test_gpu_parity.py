@@ -100,6 +100,17 @@ def test_zfactor_one_is_copy(form):
     assert torch.equal(outs[0], t)
 
 
+@pytest.mark.parametrize("g,r,model,nugget", [(2, 1, "spherical", 0.0), (3, 2, "exponential", 0.02),
+                                              (5, 2, "spherical", 0.05), (7, 1, "exponential", 0.0),
+                                              (8, 2, "exponential", 0.01)])
+def test_ds_mirror_split_geometries(g, r, model, nugget):
+    """The DS class solve splits each class system into its Z-mirror halves: odd and even g
+    (with and without a middle target), g = 2 (no difference system), nugget on and off."""
+    vol = phantoms.random_stack(4, 29, 35, g, r, k=2, seed=40 + g, model=model)
+    vol.nugget = nugget
+    _check_full(vol, "DS")
+
+
 def test_ds_fp64_solve_flag_matches():
     vol = phantoms.random_stack(5, 40, 70, 6, 2, k=2, seed=7, model="exponential")
     a, _ = _check_full(vol, "DS")
