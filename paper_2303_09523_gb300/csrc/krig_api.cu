@@ -36,8 +36,6 @@ krig_status cuda_fail(int err, const char* what)
     return fail(KRIG_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
 }
 
-int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
-
 }  // namespace
 
 void krig_internal_set_error(const char* msg) { g_last_error = msg ? msg : ""; }
@@ -303,6 +301,7 @@ static void set_chunk(krig_plan_t plan, int chunk)
         const int max_block = (V.n - 1 + V.k - 1) / V.k;
         V.chunk = chunk < 1 ? 1 : (chunk > max_block ? max_block : chunk);
         V.chunks = (max_block + V.chunk - 1) / V.chunk;
+        V.mdiv_chunks = krig_udiv_magic((uint32_t)V.chunks);
         V.item_begin = items;
         items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
     }

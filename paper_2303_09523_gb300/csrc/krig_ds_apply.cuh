@@ -402,17 +402,18 @@ __device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype
         if (P.vol[u].item_begin <= it) v = u;
     const KrigVol& V = P.vol[v];
     if (V.dtype != dtype || ds_shape(V) != shape) return false;
-    const int local = it - (int)V.item_begin;
-    const int tiles = V.tiles_x * V.tiles_y;
-    const int tile = local % tiles, rest = local / tiles;
-    const int ch = rest % V.chunks, b = rest / V.chunks;
-    const int G = V.n - 1, q = G / V.k, rm = G % V.k;
-    const int a0 = b * q + min(b, rm), a1 = (b + 1) * q + min(b + 1, rm);
+    // item = ((sub-block b) * chunks + chunk ch) * tiles + tile, divisions by multiply-high
+    const uint32_t local = (uint32_t)(it - (int)V.item_begin);
+    const uint32_t rest = krig_udiv(local, V.mdiv_tiles), tile = local - rest * (uint32_t)(V.tiles_x * V.tiles_y);
+    const uint32_t bb = krig_udiv(rest, V.mdiv_chunks), ch = rest - bb * (uint32_t)V.chunks;
+    const uint32_t ty = krig_udiv(tile, V.mdiv_tx), tx = tile - ty * (uint32_t)V.tiles_x;
+    const int b = (int)bb;
+    const int a0 = b * V.gq + min(b, V.grm), a1 = (b + 1) * V.gq + min(b + 1, V.grm);
     d.v = v;
-    d.c0 = a0 + ch * V.chunk;
+    d.c0 = a0 + (int)ch * V.chunk;
     d.c1 = min(d.c0 + V.chunk, a1);
-    d.x0 = (tile % V.tiles_x) * KRIG_TX;
-    d.y0 = (tile / V.tiles_x) * KRIG_TY;
+    d.x0 = (int)tx * KRIG_TX;
+    d.y0 = (int)ty * KRIG_TY;
     return d.c0 < d.c1;
 }
 

@@ -178,8 +178,7 @@ __device__ __forceinline__ void ds_pair(int idx, int* a, int* b)
 // evaluation per distinct lag: the in-plane part of a lag depends only on
 // (max, min) of |dx|, |dy|, and the upper-slice target lags (dz = g - t)
 // repeat the lower-slice ones (dz = t).
-__device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* gC, double* g0, double* ev, int tid,
-                             int nt)
+__device__ void ds_eval_lags(const LagDims& d, const krig_variogram& v, double* ev, int tid, int nt)
 {
     const int nCp = d.n2r * (d.n2r + 1) / 2, n0p = d.nr * (d.nr + 1) / 2;
     const int ne = 2 * nCp + (d.g - 1) * n0p;
@@ -197,6 +196,35 @@ __device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* 
         ev[e] = krig_cov(v, (double)(a * a + b * b) + dz * dz);
     }
     __syncthreads();
+}
+
+// Covariances from the distinct-lag table: between two points of the window
+// (slice s = same / other, in-plane offsets ay, ax in [0, 2r]) and between a
+// point (slice s, offsets in [0, r]) and target t.
+struct DsLags {
+    const double* ev;
+    int nCp, n0p, g;
+    __device__ __forceinline__ DsLags(const LagDims& d, const double* e)
+        : ev(e), nCp(d.n2r * (d.n2r + 1) / 2), n0p(d.nr * (d.nr + 1) / 2), g(d.g) {}
+    __device__ __forceinline__ static int pair(int ay, int ax)
+    {
+        const int a = max(ax, ay), b = min(ax, ay);
+        return a * (a + 1) / 2 + b;
+    }
+    __device__ __forceinline__ double c(int s, int ay, int ax) const { return ev[s * nCp + pair(ay, ax)]; }
+    __device__ __forceinline__ double c0(int t, int s, int ay, int ax) const
+    {
+        const int dz = s == 0 ? t : g - t;
+        return ev[2 * nCp + (dz - 1) * n0p + pair(ay, ax)];
+    }
+};
+
+// The same values expanded into the lag tables gC, g0 (layout of krig_fill_lags).
+__device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* gC, double* g0, double* ev, int tid,
+                             int nt)
+{
+    ds_eval_lags(d, v, ev, tid, nt);
+    const int nCp = d.n2r * (d.n2r + 1) / 2, n0p = d.nr * (d.nr + 1) / 2;
     const int nC = d.nC(), n0 = d.n0();
     for (int e = tid; e < nC + n0; e += nt) {
         if (e < nC) {
@@ -218,7 +246,7 @@ __device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* 
 // the identity column it turns into, so that every register index is static:
 // after n steps a row holds [X | 0 | S^-1] (up to the row's pivot, divided out
 // at the end).  No pivoting (S is SPD); a pivot that is not positive fails.
-__device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, int n2r, float* X, float* Ai, int lane)
+__device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, int n2r, double* X, float* Ai, int lane)
 {
     float r[ZL];
     const bool row = lane < n;
@@ -255,7 +283,7 @@ __device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, 
         const float di = 1.0f / dk;
 #pragma unroll
         for (int j = 0; j < ZL; ++j) {
-            if (j < m) X[lane * 8 + j] = r[j] * di;
+            if (j < m) X[lane * 8 + j] = (double)(r[j] * di);
             if (j >= ZL - n) Ai[lane * (ZN + 1) + j - (ZL - n)] = r[j] * di;
         }
     }
@@ -264,18 +292,18 @@ __device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, 
 
 // Solve, combine and write one truncation class (FP32 factorisation).
 template <int NT>
-__device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, int cx, const LagDims& d,
-                                const double* gC, const double* g0, ZSmem& S, int tid)
+__device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, int cx, const DsLags& lg, ZSmem& S,
+                                int tid)
 {
     const int warp = tid >> 5, lane = tid & 31;
     const int lx = V.xext[cx][0], rx = V.xext[cx][1], ly = V.yext[cy][0], ry = V.yext[cy][1];
     const int nx = lx + rx + 1, ny = ly + ry + 1, n = nx * ny;
-    const int n2r = d.n2r, g = V.g, r = V.r;
+    const int g = V.g, r = V.r, n2r = 2 * r + 1;
     const int hp = g / 2, hm = (g - 1) / 2;  // sum / difference targets
     const int m0 = 1 + hp, m1 = hm;  // columns of the sum / difference system
     // system entries by lag, points, right-hand sides
     for (int e = tid; e < n2r * n2r; e += NT) {
-        const double a = gC[e], b = gC[n2r * n2r + e];
+        const double a = lg.c(0, e / n2r, e % n2r), b = lg.c(1, e / n2r, e % n2r);
         S.T[0][e] = a + b;
         S.T[1][e] = a - b;
         S.Tf[0][e] = (float)(a + b);
@@ -290,8 +318,8 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
         const int ax = abs(i % nx - lx), ay = abs(i / nx - ly);
         double bp = 0.0, bm = 0.0;
         if (c == 0) bp = 2.0;
-        else if (c <= hp) bp = g0[d.i0(c, 0, ay, ax)] + g0[d.i0(c, 1, ay, ax)];
-        if (c < hm) bm = g0[d.i0(c + 1, 0, ay, ax)] - g0[d.i0(c + 1, 1, ay, ax)];
+        else if (c <= hp) bp = lg.c0(c, 0, ay, ax) + lg.c0(c, 1, ay, ax);
+        if (c < hm) bm = lg.c0(c + 1, 0, ay, ax) - lg.c0(c + 1, 1, ay, ax);
         S.B[0][i][c] = bp;
         S.B[1][i][c] = bm;
     }
@@ -300,18 +328,13 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
     // FP32 factorisation: the sum system on warp 0, the difference system on warp 1
     if (warp < 2 && (warp == 0 || m1 > 0)) {
         const int z = warp;
-        if (!ds_warp_gj(S, z, n, z ? m1 : m0, n2r, &S.R[z][0][0], &S.Ai[z][0][0], lane) && lane == 0) S.fail = 1;
+        if (!ds_warp_gj(S, z, n, z ? m1 : m0, n2r, &S.X[z][0][0], &S.Ai[z][0][0], lane) && lane == 0) S.fail = 1;
     }
     __syncthreads();
     const bool ok = !S.fail;
-    // FP64 refinement: X = X32, R = B - S X in FP64, X += S^-1 R in FP32
+    // FP64 refinement: R = B - S X in FP64, X += S^-1 R in FP32
     const int nv = n * (m0 + m1);  // (system, point, column) triples
     if (ok) {
-        for (int e = tid; e < nv; e += NT) {
-            const int z = e < n * m0 ? 0 : 1, f = z ? e - n * m0 : e, m = z ? m1 : m0;
-            S.X[z][f / m][f % m] = (double)S.R[z][f / m][f % m];
-        }
-        __syncthreads();
         // one (system, point, column) per thread: nv <= ZN * 8 <= NT
         const int z = tid < n * m0 ? 0 : 1, f = z ? tid - n * m0 : tid, m = z ? m1 : m0;
         const int i = m ? f / m : 0, c = m ? f % m : 0;
@@ -323,7 +346,6 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
                 acc = fma(-S.T[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])], S.X[z][j][c], acc);
             res = (float)acc;
         }
-        __syncthreads();
         if (tid < nv) S.R[z][i][c] = res;
         __syncthreads();
         if (tid < nv) {
@@ -351,12 +373,12 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
             double wc = 0.0;
             if (in) {
                 const int ax = abs(S.dx[lane]), ay = abs(S.dy[lane]);
-                wc = w0 * g0[d.i0(t, 0, ay, ax)] + w1 * g0[d.i0(t, 1, ay, ax)];
+                wc = w0 * lg.c0(t, 0, ay, ax) + w1 * lg.c0(t, 1, ay, ax);
                 S.W[0][lane][t - 1] = w0;
                 S.W[1][lane][t - 1] = w1;
             }
             for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-            if (lane == 0) S.var[t - 1] = gC[0] - wc - ph;
+            if (lane == 0) S.var[t - 1] = lg.c(0, 0, 0) - wc - ph;
         }
         __syncthreads();
     } else if (tid == 0) {
@@ -424,15 +446,16 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     const krig_variogram vg = P.vg[v];
     const int r = V.r;
     LagDims d{r, V.g, 2 * r + 1, r + 1};
-    ds_fill_lags(d, vg, gC, g0, ev, tid, 256);
     if (sizeof(TF) == 8) {
+        ds_fill_lags(d, vg, gC, g0, ev, tid, 256);
         SolveSmem<double, KRIG_KMAX, 8>& S = U.f64;
         const int K = ds_class_setup(V, d, g0, cy, cx, S.tap, S.Bd);
         const bool ok = team_ok_solve<double, KRIG_KMAX, 8, 256>(S, d, gC, K, V.g, tid);
         if (!ok && tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         ds_write_class(P, V, cy, cx, ok, S.Xd, S.Bd, S.tap, K, V.g, gC[0], phi, vout);
     } else {
-        ds_class_zsplit<256>(P, V, cy, cx, d, gC, g0, U.z, tid);
+        ds_eval_lags(d, vg, ev, tid, 256);
+        ds_class_zsplit<256>(P, V, cy, cx, DsLags(d, ev), U.z, tid);
     }
 }
 

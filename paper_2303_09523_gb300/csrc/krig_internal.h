@@ -25,6 +25,18 @@
 #define KRIG_DEV_SINGULAR 0x1u
 #define KRIG_DEV_TIMEOUT 0x2u
 
+// n / d for 0 <= n < 2^32 by one multiply-high with m = krig_udiv_magic(d):
+// m = ceil(2^64 / d), and floor(n m / 2^64) = floor(n / d) because the error
+// n (m d - 2^64) / (d 2^64) stays below 1/d (division by invariant integers
+// using multiplication, Granlund and Montgomery 1994).  d = 1: m = 0.
+inline uint64_t krig_udiv_magic(uint32_t d) { return d <= 1 ? 0ull : ~0ull / d + 1ull; }
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t krig_udiv(uint32_t n, uint64_t m)
+{
+    return m ? (uint32_t)__umul64hi((unsigned long long)n, (unsigned long long)m) : n;
+}
+#endif
+
 // Per-volume parameters, passed by value in the kernel parameter block.
 struct KrigVol {
     int32_t H, W, n, g, k, r, dtype;
@@ -48,7 +60,12 @@ struct KrigVol {
     int32_t n_frame;          // frame pixels (within r of the border) per slice (DS)
     int64_t frame_begin;      // first DS frame unit (32 frame pixels of one gap) of this volume
     int32_t frame_units;      // frame units per gap
+    int32_t gq;               // (n-1) / k: gaps of the smaller sub-blocks
+    int32_t grm;              // (n-1) % k: the first grm sub-blocks have one gap more
     int32_t pad0;
+    uint64_t mdiv_tiles;      // krig_udiv multipliers: by tiles_x * tiles_y,
+    uint64_t mdiv_chunks;     //   by chunks,
+    uint64_t mdiv_tx;         //   by tiles_x
     // leave-one-slice-out (plans created with KRIG_FLAG_LOO)
     int64_t loo_cls_begin;    // first LOO class block of this volume
     int64_t loo_item_begin;   // first LOO residual tile (target slices 1..n-2)
@@ -171,6 +188,11 @@ inline void krig_fill_vol(KrigVol& V, const krig_volume_desc& d, int form, int c
     const int max_block = (gaps + V.k - 1) / V.k;
     V.chunk = chunk < 1 ? 1 : (chunk > max_block ? max_block : chunk);
     V.chunks = (max_block + V.chunk - 1) / V.chunk;
+    V.gq = gaps / V.k;
+    V.grm = gaps % V.k;
+    V.mdiv_tiles = krig_udiv_magic((uint32_t)(V.tiles_x * V.tiles_y));
+    V.mdiv_chunks = krig_udiv_magic((uint32_t)V.chunks);
+    V.mdiv_tx = krig_udiv_magic((uint32_t)V.tiles_x);
     V.item_begin = *items;
     *items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
     V.cls_begin = *classes;
