@@ -38,12 +38,13 @@ template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; stati
 #define DS_WAIT_LIMIT (1u << 22)
 
 // Ring depth per input type: enough slots that the producer runs many slices
-// ahead of the consumers (a DRAM round trip spans many short gaps), within
-// about 64-80 KB of shared memory per block so two blocks fit on an SM.
+// ahead of the consumers (a DRAM round trip spans many short gaps), while the
+// ring plus the orbit-weight table of all volumes (24 KB, 48 KB for f64)
+// stays within about 100 KB of shared memory, so two blocks fit on an SM.
 template <typename TI> struct DsStages;
 template <> struct DsStages<uint16_t> { static constexpr int S = 16; };
 template <> struct DsStages<float> { static constexpr int S = 12; };
-template <> struct DsStages<double> { static constexpr int S = 6; };
+template <> struct DsStages<double> { static constexpr int S = 4; };
 
 // ---------------------------------------------------------------------------
 // mbarrier and bulk-copy primitives (inline PTX)
@@ -418,7 +419,7 @@ __device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype
 }
 
 struct DsShared {
-    void* ow;          // interior orbit weights of volumes 0..KRIG_TMA_VOLS-1, [v][2][NORB][8]
+    void* ow;          // interior orbit weights of every volume, [v][2][NORB][8]
     uint64_t* full;
     uint64_t* empty;
     uint64_t* never;  // test hook: a barrier nothing completes
@@ -435,7 +436,7 @@ template <typename TI> struct DsLayout {
     static constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;  // slot stride, elements
     static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
     static constexpr size_t bytes = bar_off + (2 * S + 2) * sizeof(uint64_t) +
-                                    (size_t)KRIG_TMA_VOLS * 2 * KRIG_NORB * KRIG_TSLOTS *
+                                    (size_t)KRIG_MAX_VOLUMES * 2 * KRIG_NORB * KRIG_TSLOTS *
                                         sizeof(typename DsTypes<TI>::TC);
     __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
     __device__ static __forceinline__ DsShared shared()
@@ -635,9 +636,8 @@ __device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsIte
     constexpr int DS_STAGES = DsStages<TI>::S;
     typedef typename DsTypes<TI>::TC TC;
     const KrigVol& V = P.vol[d.v];
-    // interior orbit weights: shared copy for the first volumes, global beyond
-    const TC* ow = d.v < KRIG_TMA_VOLS ? (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS)
-                                       : (const TC*)(P.ws + V.otab_off);
+    // interior orbit weights of the item's volume
+    const TC* ow = (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS);  // shared memory
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     // the interior orbit weights, now final, into shared memory; a named
     // barrier over the consumer warps only (the producer runs on)
     {
-        const int nv = min(P.n_vols, KRIG_TMA_VOLS);
+        const int nv = P.n_vols;
         constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
         for (int e = tid; e < nv * NW; e += DS_CONSUMERS * 32) {
             const KrigVol& Vv = P.vol[e / NW];
