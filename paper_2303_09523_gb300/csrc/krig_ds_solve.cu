@@ -140,25 +140,8 @@ __device__ __forceinline__ int ds_class_setup(const KrigVol& V, const LagDims& d
 // u = C^-1 c0, v = C^-1 1, phi = (1'u - 1) / (1'v), w = u - phi v and the
 // kriging variance C(0) - w'c0 - phi.
 // ---------------------------------------------------------------------------
-constexpr int ZN = (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1);  // in-plane points, <= 25
-constexpr int ZL = 32;                                         // register row: n + m <= 25 + 5
-static_assert(ZN + 1 + KRIG_GMAX / 2 <= ZL, "register row too short");
-static_assert(ZN * 8 <= 256, "one refinement entry per thread");
 // distinct lags: (a >= b) pairs in [0, 2r] for dz = 0 and g, in [0, r] for dz = 1..g-1
 constexpr int ZEV = (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 2) + (KRIG_GMAX - 1) * (KRIG_RMAX + 1) * (KRIG_RMAX + 2) / 2;
-
-struct ZSmem {
-    double T[2][ZN];          // A + B, A - B entries by in-plane lag ay * (2r+1) + ax
-    float Tf[2][ZN];
-    double B[2][ZN][8];       // right-hand sides
-    double X[2][ZN][8];       // solutions
-    float R[2][ZN][8];        // FP64 residuals rounded to FP32
-    float Ai[2][ZN][ZN + 1];  // FP32 inverses, padded rows
-    double W[2][ZN][8];       // weights: [slice][point][t-1]
-    double var[8];            // kriging variance per target
-    int8_t dx[ZL], dy[ZL];
-    int fail;
-};
 
 union DsSolveSmem {
     SolveSmem<double, KRIG_KMAX, 8> f64;
@@ -239,55 +222,6 @@ __device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* 
         }
     }
     __syncthreads();
-}
-
-// Gauss-Jordan on [S | B] by one warp, lane i holding row i in registers.
-// Each step drops the pivot column from the front of every row and appends
-// the identity column it turns into, so that every register index is static:
-// after n steps a row holds [X | 0 | S^-1] (up to the row's pivot, divided out
-// at the end).  No pivoting (S is SPD); a pivot that is not positive fails.
-__device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, int n2r, double* X, float* Ai, int lane)
-{
-    float r[ZL];
-    const bool row = lane < n;
-    const int dxi = row ? S.dx[lane] : 0, dyi = row ? S.dy[lane] : 0;
-#pragma unroll
-    for (int j = 0; j < ZL; ++j) {
-        float a = 0.0f;
-        if (row) {
-            if (j < n) a = S.Tf[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])];
-            else if (j < n + m) a = (float)S.B[z][lane][j - n];
-        }
-        r[j] = a;
-    }
-    float dk = 1.0f;
-    bool ok = true;
-    for (int k = 0; k < n; ++k) {
-        const float p0 = __shfl_sync(0xffffffffu, r[0], k);
-        if (!(p0 > 0.0f)) {  // the same value in every lane
-            ok = false;
-            break;
-        }
-        const bool piv = lane == k;
-        const float fi = r[0] * __frcp_rn(p0);
-        const float f = piv ? 0.0f : fi;
-        if (piv) dk = p0;
-#pragma unroll
-        for (int j = 0; j + 1 < ZL; ++j) {
-            const float pj = __shfl_sync(0xffffffffu, r[j + 1], k);
-            r[j] = fmaf(-f, pj, r[j + 1]);
-        }
-        r[ZL - 1] = piv ? 1.0f : -fi;
-    }
-    if (ok && row) {
-        const float di = 1.0f / dk;
-#pragma unroll
-        for (int j = 0; j < ZL; ++j) {
-            if (j < m) X[lane * 8 + j] = (double)(r[j] * di);
-            if (j >= ZL - n) Ai[lane * (ZN + 1) + j - (ZL - n)] = r[j] * di;
-        }
-    }
-    return ok;
 }
 
 // Solve, combine and write one truncation class (FP32 factorisation).

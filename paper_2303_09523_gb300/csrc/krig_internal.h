@@ -71,9 +71,9 @@ struct KrigVol {
     int64_t loo_item_begin;   // first LOO residual tile (target slices 1..n-2)
     int64_t loo_adj_begin;    // first LOO adjoint tile (slices 0..n-1)
     int64_t lw_off;           // LOO weights [ncy][ncx][2][2r+1][2r+1] float
-    int64_t lbar_off;         // sum r S_k per class tap, same layout, double
+    int64_t lbar_off;         // sum r S_k per class tap, same layout, double, KRIG_LOO_REP copies
     int64_t res_off;          // residuals (n-2) x H x W float
-    int64_t lacc_off;         // loss accumulator, double
+    int64_t lacc_off;         // loss accumulators, KRIG_LOO_REP doubles
 };
 
 struct KrigLaunch {
@@ -215,7 +215,11 @@ inline void krig_fill_vol(KrigVol& V, const krig_volume_desc& d, int form, int c
     V.pad0 = 0;
 }
 
-// Leave-one-slice-out tables of one volume (plans with KRIG_FLAG_LOO).
+// Leave-one-slice-out tables of one volume (plans with KRIG_FLAG_LOO).  The
+// residual blocks add their loss and tap-sum partials into one of
+// KRIG_LOO_REP copies (block index modulo KRIG_LOO_REP), so that no address
+// takes more than a few dozen atomic adds; the readers sum the copies.
+#define KRIG_LOO_REP 32
 inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* items, int64_t* adj)
 {
     const auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
@@ -231,11 +235,11 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     V.lw_off = *off;
     *off = up(*off + ncls * taps * 4);
     V.lbar_off = *off;
-    *off = up(*off + ncls * taps * 8);
+    *off = up(*off + KRIG_LOO_REP * ncls * taps * 8);
     V.res_off = *off;
     *off = up(*off + (int64_t)(V.n - 2) * V.H * V.W * 4);
     V.lacc_off = *off;
-    *off = up(*off + 8);
+    *off = up(*off + KRIG_LOO_REP * 8);
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times

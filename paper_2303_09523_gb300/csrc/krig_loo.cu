@@ -55,15 +55,23 @@ __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2
 // ---------------------------------------------------------------------------
 // Class kernel: one block per (volume, xy-class).  mode 0: LOO weights.
 // mode 1: weights and the adjoint contribution of this class to dL/dtheta.
+//
+// The two bracketing slices carry the same window and sit symmetrically
+// (dz = -g, +g) about the target, so with C = [A B; B A] (B across dz = 2g)
+// both right-hand sides c0 = [c; c] and 1 are symmetric: only the sum system
+// (A + B) s = b0 + b1 is needed, and w0 = w1 = (s_u - phi s_v) / 2.  For
+// dL/dtheta, sum_i abar_i (dc0_i - (dC w)_i) runs over both slices with equal
+// brackets, so only abar_lower + abar_upper = s_x - (1's_x / 1's_v) s_v enters,
+// with s_x from the same sum system at right-hand side wbar_lower + wbar_upper.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigLaunch P, int mode)
 {
-    __shared__ GJSmem S;
+    __shared__ ZSmem S;
     __shared__ double gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
     __shared__ double g0[2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
     __shared__ double dC[3][2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
     __shared__ double d0[3][2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
-    __shared__ double wgt[KRIG_KMAX], abar[KRIG_KMAX], red[8][4];
+    __shared__ double wgt[ZN], abar[ZN], red[8][4];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int v = 0;
@@ -75,7 +83,6 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     const krig_variogram vg = P.vg[v];
     const int r = V.r, n2r = 2 * r + 1, nr = r + 1;
     const int g2 = 2 * V.g;  // LOO: bracketing slices 2g apart, target in the middle
-    LagDims d{r, g2, n2r, nr};
     const int nC = 2 * n2r * n2r, n0 = 2 * nr * nr;
     for (int e = tid; e < nC + n0; e += 256) {
         double h2, dd[3];
@@ -97,88 +104,106 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     __syncthreads();
     const int lx = V.xext[cx][0], rx = V.xext[cx][1], ly = V.yext[cy][0], ry = V.yext[cy][1];
     const int nx = lx + rx + 1, ny = ly + ry + 1;
-    const int K = 2 * nx * ny;
-    const int NC = mode == 0 ? 2 : 3;  // c0, ones, [wbar]
-    const double* lbar = (const double*)(P.ws + V.lbar_off) + (int64_t)local * (2 * n2r * n2r);
+    const int n = nx * ny;                // in-plane points (per slice)
+    const int m = mode == 0 ? 2 : 3;      // right-hand sides: 2c, 2 (ones), [wbar_lo + wbar_up]
+    const int nn = n2r * n2r;
+    const double* lbar = (const double*)(P.ws + V.lbar_off) + (int64_t)local * (2 * nn);
+    const int64_t lrep = (int64_t)V.ncx * V.ncy * (2 * nn);  // stride between the copies
     const double coef = mode == 0 ? 0.0 : 2.0 * P.grad_loss[v] / ((double)(V.n - 2) * V.H * V.W);
-    for (int i = tid; i < K; i += 256) {
-        Tap tp;
-        tp.s = (int8_t)(i / (nx * ny));
-        tp.dy = (int8_t)((i / nx) % ny - ly);
-        tp.dx = (int8_t)(i % nx - lx);
-        tp.pad = 0;
-        S.tap[i] = tp;
-        S.Bd[i * 8 + 0] = g0[(tp.s * nr + abs((int)tp.dy)) * nr + abs((int)tp.dx)];
-        S.Bd[i * 8 + 1] = 1.0;
+    for (int e = tid; e < nn; e += 256) {
+        const double a = gC[e] + gC[nn + e];  // A + B at in-plane lag e
+        S.T[0][e] = a;
+        S.Tf[0][e] = (float)a;
+    }
+    for (int e = tid; e < ZL; e += 256) {
+        S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
+        S.dy[e] = (int8_t)(e < n ? e / nx - ly : 0);
+    }
+    for (int i = tid; i < n; i += 256) {
+        const int dx = i % nx - lx, dy = i / nx - ly;
+        S.B[0][i][0] = 2.0 * g0[abs(dy) * nr + abs(dx)];
+        S.B[0][i][1] = 2.0;
         if (mode == 1) {
-            const int full = (tp.s * n2r + (tp.dy + r)) * n2r + (tp.dx + r);
-            S.Bd[i * 8 + 2] = coef * lbar[full];  // wbar = 2 gL / N * sum r S_k
+            double sum = 0.0;
+            for (int s = 0; s < 2; ++s) {
+                const int full = (s * n2r + (dy + r)) * n2r + (dx + r);
+                for (int c = 0; c < KRIG_LOO_REP; ++c) sum += lbar[c * lrep + full];
+            }
+            S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
         }
     }
+    if (tid == 0) S.fail = 0;
     __syncthreads();
-    const bool ok = block_gj_solve<256>(S, d, gC, K, NC, tid);
-    if (!ok) {
+    if (warp == 0 && !ds_warp_gj(S, 0, n, m, n2r, &S.X[0][0][0], &S.Ai[0][0][0], lane) && lane == 0) S.fail = 1;
+    __syncthreads();
+    if (S.fail) {
         if (tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         return;
     }
-    // sums over the taps: 1'u, 1'v, 1'x
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = tid; i < K; i += 256) {
-        s0 += S.Xd[i * 8 + 0];
-        s1 += S.Xd[i * 8 + 1];
-        if (mode == 1) s2 += S.Xd[i * 8 + 2];
+    // FP64 refinement: R = B - (A+B) X, X += (A+B)^-1 R
+    const int nv = n * m;
+    {
+        const int i = tid / m, c = tid % m;
+        if (tid < nv) {
+            double acc = S.B[0][i][c];
+            for (int j = 0; j < n; ++j)
+                acc = fma(-S.T[0][abs(S.dy[i] - S.dy[j]) * n2r + abs(S.dx[i] - S.dx[j])], S.X[0][j][c], acc);
+            S.R[0][i][c] = (float)acc;
+        }
+        __syncthreads();
+        if (tid < nv) {
+            float corr = 0.0f;
+            for (int j = 0; j < n; ++j) corr = fmaf(S.Ai[0][i][j], S.R[0][j][c], corr);
+            S.X[0][i][c] += (double)corr;
+        }
+        __syncthreads();
     }
-    for (int o = 16; o; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) {
-        red[warp][0] = s0;
-        red[warp][1] = s1;
-        red[warp][2] = s2;
-    }
-    __syncthreads();
-    double su = 0.0, sv = 0.0, sx = 0.0;
-    for (int w = 0; w < 8; ++w) {
-        su += red[w][0];
-        sv += red[w][1];
-        sx += red[w][2];
-    }
-    const double phi = (su - 1.0) / sv;
-    const double aphi = sx / sv;
-    for (int i = tid; i < K; i += 256) {
-        wgt[i] = S.Xd[i * 8 + 0] - phi * S.Xd[i * 8 + 1];
-        if (mode == 1) abar[i] = S.Xd[i * 8 + 2] - aphi * S.Xd[i * 8 + 1];
+    // sums over the points (one warp: n <= 32): 1's_u, 1's_v, 1's_x
+    if (warp == 0) {
+        double su = 0.0, sv = 0.0, sx = 0.0;
+        if (lane < n) {
+            su = S.X[0][lane][0];
+            sv = S.X[0][lane][1];
+            if (mode == 1) sx = S.X[0][lane][2];
+        }
+        for (int o = 16; o; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        }
+        const double phi = (su - 1.0) / sv, aphi = sx / sv;
+        if (lane < n) {
+            wgt[lane] = 0.5 * (S.X[0][lane][0] - phi * S.X[0][lane][1]);
+            if (mode == 1) abar[lane] = S.X[0][lane][2] - aphi * S.X[0][lane][1];
+        }
     }
     __syncthreads();
     if (mode == 0) {
-        // LOO weight row in the full tap layout [s][dy+r][dx+r], zeros on truncated taps
-        float* lw = (float*)(P.ws + V.lw_off) + (int64_t)local * (2 * n2r * n2r);
-        for (int f = tid; f < 2 * n2r * n2r; f += 256) {
-            const int dx = f % n2r - r, dy = (f / n2r) % n2r - r, s = f / (n2r * n2r);
+        // LOO weight row in the full tap layout [s][dy+r][dx+r] (the same in both
+        // slices), zeros on truncated taps
+        float* lw = (float*)(P.ws + V.lw_off) + (int64_t)local * (2 * nn);
+        for (int f = tid; f < 2 * nn; f += 256) {
+            const int dx = f % n2r - r, dy = (f / n2r) % n2r - r;
             float w = 0.0f;
-            if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = (float)wgt[(s * ny + (dy + ly)) * nx + (dx + lx)];
+            if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = (float)wgt[(dy + ly) * nx + (dx + lx)];
             lw[f] = w;
         }
         return;
     }
-    // dL/dtheta_p = abar' (dc0/dtheta_p - dC/dtheta_p w), one term per (i, p)
+    // dL/dtheta_p = sum_i abar_i (dc0_i/dtheta_p - sum_j d(A+B)_ij/dtheta_p w_j), i, j over the points
     double tp3[3] = {0.0, 0.0, 0.0};
-    for (int i = tid; i < K; i += 256) {
-        const Tap ti = S.tap[i];
-        const int i0 = (ti.s * nr + abs((int)ti.dy)) * nr + abs((int)ti.dx);
+    for (int i = tid; i < n; i += 256) {
+        const int dxi = S.dx[i], dyi = S.dy[i];
+        const int i0 = abs(dyi) * nr + abs(dxi);
         double acc[3] = {d0[0][i0], d0[1][i0], d0[2][i0]};
-        for (int j = 0; j < K; ++j) {
-            const Tap tj = S.tap[j];
-            const int ic = d.iC(ti.s != tj.s, abs(ti.dy - tj.dy), abs(ti.dx - tj.dx));
-            for (int p = 0; p < 3; ++p) acc[p] -= dC[p][ic] * wgt[j];
+        for (int j = 0; j < n; ++j) {
+            const int ic = abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j]);
+            for (int p = 0; p < 3; ++p) acc[p] -= (dC[p][ic] + dC[p][nn + ic]) * wgt[j];
         }
         for (int p = 0; p < 3; ++p) tp3[p] += abar[i] * acc[p];
     }
     for (int p = 0; p < 3; ++p)
         for (int o = 16; o; o >>= 1) tp3[p] += __shfl_xor_sync(0xffffffffu, tp3[p], o);
-    __syncthreads();
     if (lane == 0)
         for (int p = 0; p < 3; ++p) red[warp][p] = tp3[p];
     __syncthreads();
@@ -214,6 +239,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     float* ce = hi + ROWS * LOO_RP;                  // LOO_TY x LOO_TX, target slice
     float* sg = ce + LOO_TY * LOO_TX;                // [ncls][NTAP] tap sums (mode 1)
     double* sl = (double*)(sg + 32 * NTAP + 2);      // loss partials of the warps (8)
+    float* wsm = (float*)(sl + 8);                   // [ncls][NTAP] LOO weights
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncls = V.ncx * V.ncy;
     for (int e = tid; e < ROWS * LOO_RP; e += 256) {
@@ -233,11 +259,15 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     }
     if (mode == 1)
         for (int e = tid; e < ncls * NTAP; e += 256) sg[e] = 0.f;
+    {
+        const float* lwg = (const float*)(P.ws + V.lw_off);
+        for (int e = tid; e < ncls * NTAP; e += 256) wsm[e] = lwg[e];
+    }
     __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int y = y0 + lrow;
-    const float* lw = (const float*)(P.ws + V.lw_off);
+    const float* lw = wsm;
     float gi[NTAP];
 #pragma unroll
     for (int k = 0; k < NTAP; ++k) gi[k] = 0.f;
@@ -260,7 +290,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
                         const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
                         const float z = (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx];
                         taps[k] = z;
-                        pred = fmaf(__ldg(wr + k), z, pred);
+                        pred = fmaf(wr[k], z, pred);
                     }
             const float res = pred - ce[lrow * LOO_TX + lcol + p];
             loss += (double)res * (double)res;
@@ -291,19 +321,23 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
         }
     }
     __syncthreads();
+    const int rep = (int)(blockIdx.x % KRIG_LOO_REP);
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += sl[w];
-        atomicAdd((double*)(P.ws + V.lacc_off), s);
+        atomicAdd((double*)(P.ws + V.lacc_off) + rep, s);
     }
     if (mode == 1) {
-        double* lbar = (double*)(P.ws + V.lbar_off);
+        double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * NTAP;
         for (int e = tid; e < ncls * NTAP; e += 256)
             if (sg[e] != 0.f) atomicAdd(lbar + e, (double)sg[e]);
     }
 }
 
-__global__ void __launch_bounds__(256) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
+// One instance per half-width r (the tap arrays set the register budget);
+// blocks of volumes with another r leave at once.
+template <int R>
+__global__ void __launch_bounds__(256, R == 2 ? 2 : 4) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
 {
     extern __shared__ __align__(16) float lsm[];
     const int64_t it = blockIdx.x;
@@ -316,11 +350,7 @@ __global__ void __launch_bounds__(256) k_loo_residual(const __grid_constant__ Kr
     const int j = 1 + (int)(local / tiles);
     const int tile = (int)(local % tiles);
     const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
-    switch (V.r) {
-    case 0: loo_residual_tile<0>(P, v, j, x0, y0, mode, lsm); break;
-    case 1: loo_residual_tile<1>(P, v, j, x0, y0, mode, lsm); break;
-    default: loo_residual_tile<2>(P, v, j, x0, y0, mode, lsm); break;
-    }
+    if (V.r == R) loo_residual_tile<R>(P, v, j, x0, y0, mode, lsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,6 +367,7 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     const float* res = (const float*)(P.ws + V.res_off);  // r_j at (j-1)
     float* rup = sm;                   // r_{m+1}: predictions for which S_m is the lower slice
     float* rdn = sm + ROWS * LOO_RP;   // r_{m-1}: predictions for which S_m is the upper slice
+    float* wsm = rdn + ROWS * LOO_RP;  // [ncls][NTAP] LOO weights
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool has_up = m + 1 <= n - 2, has_dn = m - 1 >= 1;
     for (int e = tid; e < ROWS * LOO_RP; e += 256) {
@@ -350,12 +381,16 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
         rup[e] = a;
         rdn[e] = b;
     }
+    {
+        const float* lwg = (const float*)(P.ws + V.lw_off);
+        for (int e = tid; e < V.ncx * V.ncy * NTAP; e += 256) wsm[e] = lwg[e];
+    }
     __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int y = y0 + lrow;
     if (y >= H) return;
-    const float* lw = (const float*)(P.ws + V.lw_off);
+    const float* lw = wsm;
     const double coef = 2.0 * P.grad_loss[v] / ((double)(n - 2) * H * W);
     float* gs = P.grad_slices[v];
     for (int p = 0; p < 4; ++p) {
@@ -373,8 +408,8 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
                 if (qx < 0 || qx >= W) continue;
                 const float* wr = lw + (int64_t)(cyq * V.ncx + V.xmap[krig_slot(qx, W, R)]) * NTAP;
                 const int off = (lrow + R - dy) * LOO_RP + LOO_PAD + lcol + p - dx;
-                acc = fmaf(__ldg(wr + (0 * N2R + (dy + R)) * N2R + (dx + R)), rup[off], acc);  // S_m lower of m+1
-                acc = fmaf(__ldg(wr + (1 * N2R + (dy + R)) * N2R + (dx + R)), rdn[off], acc);  // S_m upper of m-1
+                acc = fmaf(wr[(0 * N2R + (dy + R)) * N2R + (dx + R)], rup[off], acc);  // S_m lower of m+1
+                acc = fmaf(wr[(1 * N2R + (dy + R)) * N2R + (dx + R)], rdn[off], acc);  // S_m upper of m-1
             }
         }
         double gval = (double)acc;
@@ -386,7 +421,8 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     }
 }
 
-__global__ void __launch_bounds__(256) k_loo_adjoint(const __grid_constant__ KrigLaunch P)
+template <int R>
+__global__ void __launch_bounds__(256, R == 2 ? 2 : 4) k_loo_adjoint(const __grid_constant__ KrigLaunch P)
 {
     extern __shared__ __align__(16) float lsm[];
     const int64_t it = blockIdx.x;
@@ -400,11 +436,7 @@ __global__ void __launch_bounds__(256) k_loo_adjoint(const __grid_constant__ Kri
     const int m = (int)(local / tiles);
     const int tile = (int)(local % tiles);
     const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
-    switch (V.r) {
-    case 0: loo_adjoint_tile<0>(P, v, m, x0, y0, lsm); break;
-    case 1: loo_adjoint_tile<1>(P, v, m, x0, y0, lsm); break;
-    default: loo_adjoint_tile<2>(P, v, m, x0, y0, lsm); break;
-    }
+    if (V.r == R) loo_adjoint_tile<R>(P, v, m, x0, y0, lsm);
 }
 
 __global__ void k_loo_finalize(const __grid_constant__ KrigLaunch P)
@@ -412,7 +444,10 @@ __global__ void k_loo_finalize(const __grid_constant__ KrigLaunch P)
     const int v = threadIdx.x;
     if (v >= P.n_vols) return;
     const KrigVol& V = P.vol[v];
-    P.loss[v] = *(const double*)(P.ws + V.lacc_off) / ((double)(V.n - 2) * V.H * V.W);
+    const double* acc = (const double*)(P.ws + V.lacc_off);
+    double s = 0.0;
+    for (int c = 0; c < KRIG_LOO_REP; ++c) s += acc[c];
+    P.loss[v] = s / ((double)(V.n - 2) * V.H * V.W);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,8 +460,10 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
         const int r = L.vol[v].r;
         const int rows = LOO_TY + 2 * r;
         const int ntap = 2 * (2 * r + 1) * (2 * r + 1);
-        size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4
-                           : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + (32 * ntap + 2) * 4 + 8 * 8 + 16;
+        const size_t ncls = (size_t)L.vol[v].ncx * L.vol[v].ncy;
+        size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4 + ncls * ntap * 4
+                           : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + (32 * ntap + 2) * 4 + 8 * 8 +
+                                 ncls * ntap * 4 + 16;
         if (b > m) m = b;
     }
     return m;
@@ -439,28 +476,39 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
     // zero the loss accumulators and (backward) the tap sums
     for (int v = 0; v < L.n_vols; ++v) {
         const KrigVol& V = L.vol[v];
-        e = cudaMemsetAsync(L.ws + V.lacc_off, 0, sizeof(double), st);
+        e = cudaMemsetAsync(L.ws + V.lacc_off, 0, KRIG_LOO_REP * sizeof(double), st);
         if (e != cudaSuccess) return (int)e;
         if (backward) {
-            const size_t nb = (size_t)V.ncx * V.ncy * 2 * (2 * V.r + 1) * (2 * V.r + 1) * sizeof(double);
+            const size_t nb = (size_t)KRIG_LOO_REP * V.ncx * V.ncy * 2 * (2 * V.r + 1) * (2 * V.r + 1) * sizeof(double);
             e = cudaMemsetAsync(L.ws + V.lbar_off, 0, nb, st);
             if (e != cudaSuccess) return (int)e;
         }
     }
     k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    bool has_r[KRIG_RMAX + 1] = {};
+    for (int v = 0; v < L.n_vols; ++v) has_r[L.vol[v].r] = true;
     const size_t s1 = loo_smem(L, 0);
-    if (s1 > 48 * 1024) cudaFuncSetAttribute(k_loo_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-    k_loo_residual<<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    for (int r = 0; r <= KRIG_RMAX; ++r) {
+        if (!has_r[r]) continue;
+        if (r == 0) k_loo_residual<0><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
+        else if (r == 1) k_loo_residual<1><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
+        else k_loo_residual<2><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    }
     if (!backward) {
         k_loo_finalize<<<1, 64, 0, st>>>(L);
         return (int)cudaGetLastError();
     }
     if (want_grad_slices) {
         const size_t s2 = loo_smem(L, 1);
-        k_loo_adjoint<<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
-        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        for (int r = 0; r <= KRIG_RMAX; ++r) {
+            if (!has_r[r]) continue;
+            if (r == 0) k_loo_adjoint<0><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
+            else if (r == 1) k_loo_adjoint<1><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
+            else k_loo_adjoint<2><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
+            if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        }
     }
     if (want_grad_params) {
         k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, 1);
