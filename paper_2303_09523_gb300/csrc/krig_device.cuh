@@ -337,93 +337,6 @@ __device__ __forceinline__ void warp_sweep(const T* Ls, const T* dinv, T (&x)[Re
     });
 }
 
-// Shared memory of one block-wide class solve with the register factorisation.
-template <int KM>
-struct RegSolveSmem {
-    float Ls[KM * (KM + 1)];
-    float dinv[KM];
-    float Xf[KM * 8];      // float staging of right-hand sides / residuals
-    double Bd[KM * 8];     // FP64 right-hand sides
-    double Xd[KM * 8];     // FP64 solutions
-    Tap tap[KM];
-    int flag;
-};
-
-// Block-wide (NT threads, NT/32 >= NC warps) ordinary-kriging solve of one
-// geometry class with the register factorisation: warp 0 factors C in FP32,
-// warp c sweeps right-hand side c, all threads form the FP64 residual
-// B - C X, the warps sweep the correction, and S.Xd receives the refined
-// FP64 solution.  Taps beyond K are identity-padded.  C comes from the FP64
-// lag table gC.  Returns false if C was not positive definite.
-template <int KM, int NT>
-__device__ bool block_ok_solve_reg(RegSolveSmem<KM>& S, const LagDims& d, const double* gC, int K, int NC, int tid)
-{
-    constexpr int ROWS = RegDim<KM>::ROWS;
-    const int warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        float a[ROWS][KM];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = lane + 32 * q;
-            const Tap ti = S.tap[i < K ? i : 0];
-#pragma unroll
-            for (int j = 0; j < KM; ++j) {
-                float v;
-                if (i < K && j < K) v = (float)krig_cij(d, gC, ti, S.tap[j]);
-                else v = (i == j) ? 1.0f : 0.0f;
-                a[q][j] = v;
-            }
-        }
-        const bool ok = warp_chol_reg<KM>(a, lane);
-        if (ok) warp_store_factor<KM>(a, S.Ls, S.dinv, lane);
-        if (lane == 0) S.flag = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (!S.flag) return false;
-    // first solve, one warp per right-hand side
-    if (warp < NC) {
-        float x[ROWS];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = lane + 32 * q;
-            x[q] = i < K ? (float)S.Bd[i * 8 + warp] : 0.0f;
-        }
-        warp_sweep<KM>(S.Ls, S.dinv, x, lane);
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = lane + 32 * q;
-            if (i < K) S.Xd[i * 8 + warp] = (double)x[q];
-        }
-    }
-    __syncthreads();
-    // FP64 residual of every column
-    for (int e = tid; e < K * NC; e += NT) {
-        const int i = e / NC, c = e % NC;
-        double s = S.Bd[i * 8 + c];
-        const Tap ti = S.tap[i];
-        for (int j = 0; j < K; ++j) s -= krig_cij(d, gC, ti, S.tap[j]) * S.Xd[j * 8 + c];
-        S.Xf[i * 8 + c] = (float)s;
-    }
-    __syncthreads();
-    // correction solve and update
-    if (warp < NC) {
-        float x[ROWS];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = lane + 32 * q;
-            x[q] = i < K ? S.Xf[i * 8 + warp] : 0.0f;
-        }
-        warp_sweep<KM>(S.Ls, S.dinv, x, lane);
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = lane + 32 * q;
-            if (i < K) S.Xd[i * 8 + warp] += (double)x[q];
-        }
-    }
-    __syncthreads();
-    return true;
-}
-
 // Per-warp shared memory of a per-voxel solve (two right-hand sides: c0 and ones).
 template <int KM, typename T>
 struct VoxSmem {
@@ -506,113 +419,6 @@ __device__ bool warp_ok_solve_vox(VoxSmem<KM, T>& S, const LagDims& d, const dou
         }
         __syncwarp();
     }
-    return true;
-}
-
-// ---------------------------------------------------------------------------
-// Block-parallel inversion for the class solves.
-//
-// Gauss-Jordan elimination of [C | I] in FP32 shared memory by the whole
-// block, without row scaling: at step k every row i != k subtracts
-// (a_ik / a_kk) times row k over the columns that can still be nonzero
-// (k+1..K-1 of the left half, 0..k of the right half), so one barrier per
-// step suffices.  C is SPD, so diagonal pivots are positive and no pivoting
-// is needed.  Afterwards row i of C^-1 is the right half of row i divided by
-// a_ii.  With C^-1 explicit, the solve X = C^-1 B and the correction of the
-// FP64 iterative-refinement step, X += C^-1 (B - C X), are parallel
-// matrix-vector products instead of sequential triangular sweeps, and the
-// code stays a few compact loops (a cold instruction cache is the latency
-// limit of a kernel that runs once per call).
-// ---------------------------------------------------------------------------
-struct GJSmem {
-    static constexpr int LDA = 2 * KRIG_KMAX + 1;  // odd: conflict-free column access
-    float A[KRIG_KMAX * LDA];
-    float Xf[KRIG_KMAX * 8];
-    double Bd[KRIG_KMAX * 8];
-    double Xd[KRIG_KMAX * 8];
-    Tap tap[KRIG_KMAX];
-    int flag;
-};
-
-template <int NT>
-__device__ bool block_gj_solve(GJSmem& S, const LagDims& d, const double* gC, int K, int NC, int tid)
-{
-    constexpr int LDA = GJSmem::LDA;
-    float* A = S.A;
-    for (int e = tid; e < K * K; e += NT) {
-        const int i = e / K, j = e % K;
-        A[i * LDA + j] = (float)krig_cij(d, gC, S.tap[i], S.tap[j]);
-        A[i * LDA + K + j] = (i == j) ? 1.0f : 0.0f;
-    }
-    if (tid == 0) S.flag = 1;
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int RW = (KRIG_KMAX + NT / 32 - 1) / (NT / 32);  // rows per warp
-    for (int k = 0; k < K; ++k) {
-        const float piv = A[k * LDA + k];
-        if (!(piv > 0.0f)) {  // uniform: every thread reads the same pivot
-            if (tid == 0) S.flag = 0;
-            break;
-        }
-        const float ip = __frcp_rn(piv);
-        // rows over warps, the K columns that can still be nonzero over lanes
-        // (left k+1..K-1, right K..K+k).  All operands are read before any
-        // write: within a step no element is both read and written.
-        const int nl = K - 1 - k;
-        const int j0 = lane < nl ? k + 1 + lane : K + (lane - nl);
-        const int j1 = lane + 32 < nl ? k + 33 + lane : K + (lane + 32 - nl);
-        const bool c0 = lane < K, c1 = lane + 32 < K;
-        const float rk0 = c0 ? A[k * LDA + j0] : 0.0f, rk1 = c1 ? A[k * LDA + j1] : 0.0f;
-        float f[RW];
-#pragma unroll
-        for (int q = 0; q < RW; ++q) {
-            const int i = warp + q * (NT / 32);
-            f[q] = (i < K && i != k) ? A[i * LDA + k] * ip : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < RW; ++q) {
-            const int i = warp + q * (NT / 32);
-            if (i < K && i != k) {
-                if (c0) A[i * LDA + j0] = fmaf(-f[q], rk0, A[i * LDA + j0]);
-                if (c1) A[i * LDA + j1] = fmaf(-f[q], rk1, A[i * LDA + j1]);
-            }
-        }
-        __syncthreads();
-    }
-    __syncthreads();
-    if (!S.flag) return false;
-    // C^-1 in place: right half of row i divided by its pivot
-    for (int e = tid; e < K * K; e += NT) {
-        const int i = e / K, j = e % K;
-        A[i * LDA + K + j] *= 1.0f / A[i * LDA + i];
-    }
-    __syncthreads();
-    const float* Ci = A + K;  // C^-1 with leading dimension LDA
-    // X = C^-1 B (FP32), kept in FP64
-    for (int e = tid; e < K * NC; e += NT) {
-        const int i = e / NC, c = e % NC;
-        float s = 0.0f;
-        for (int j = 0; j < K; ++j) s = fmaf(Ci[i * LDA + j], (float)S.Bd[j * 8 + c], s);
-        S.Xd[i * 8 + c] = (double)s;
-    }
-    __syncthreads();
-    // FP64 residual R = B - C X
-    for (int e = tid; e < K * NC; e += NT) {
-        const int i = e / NC, c = e % NC;
-        double s = S.Bd[i * 8 + c];
-        const Tap ti = S.tap[i];
-        for (int j = 0; j < K; ++j) s -= krig_cij(d, gC, ti, S.tap[j]) * S.Xd[j * 8 + c];
-        S.Xf[i * 8 + c] = (float)s;
-    }
-    __syncthreads();
-    // correction X += C^-1 R
-    for (int e = tid; e < K * NC; e += NT) {
-        const int i = e / NC, c = e % NC;
-        float s = 0.0f;
-        for (int j = 0; j < K; ++j) s = fmaf(Ci[i * LDA + j], S.Xf[j * 8 + c], s);
-        S.Xd[i * 8 + c] += (double)s;
-    }
-    __syncthreads();
     return true;
 }
 
