@@ -91,7 +91,7 @@ __device__ __forceinline__ bool voxel_solve(unsigned char* raw, const LagDims& d
 }
 
 template <typename TF, int RMAX>
-__global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunch P)
+__global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunch P, int rmin)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunc
         const int y = (int)(pix / V.W), x = (int)(pix % V.W);
         const int g = V.g, j = z / g, t = z % g;
         const bool f64 = V.dtype == KRIG_F64;
+        if (V.r < rmin) continue;  // voxel of the one-voxel-per-lane kernel
         if (t == 0) {  // known slice: copy through
             if (lane == 0) {
                 double val = in_value(P.in[v], V.dtype, V.scale, (int64_t)j * plane + pix);
@@ -166,8 +167,152 @@ __global__ void __launch_bounds__(256) k_voxel(const __grid_constant__ KrigLaunc
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// P64 for windows of up to 18 points (r <= 1): one voxel per lane.  A warp
+// of FP64 work per voxel leaves most lanes idle on an 18-point system; here
+// every lane factors its own voxel's system, so each FP64 instruction does
+// 32 voxels' work.  LDL' factorisation (C is SPD, no pivoting) of the lower
+// triangle in shared memory, interleaved [element][lane] so that the lanes
+// of a warp touch consecutive words; u = C^-1 c0 and v = C^-1 1 by forward,
+// diagonal and backward sweeps, then phi, w, the estimate and the variance as
+// in the warp kernel.  The voxel's result does not depend on which other
+// volumes share the launch.
+// ---------------------------------------------------------------------------
+constexpr int LK = 18, LT = LK * (LK + 1) / 2;  // points, lower-triangle entries
+constexpr int LWARPS = 4;                       // warps per block
+constexpr size_t LSMEM = (size_t)LWARPS * (LT + 2 * LK) * 32 * sizeof(double);
+
+__global__ void __launch_bounds__(LWARPS * 32, 1) k_voxel_lane(const __grid_constant__ KrigLaunch P)
+{
+    extern __shared__ __align__(16) double lsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* const Lm = lsm + (size_t)warp * (LT + 2 * LK) * 32;
+    double* const bu = Lm + LT * 32;
+    double* const bv = bu + LK * 32;
+#define LE(e) Lm[(e) * 32 + lane]
+#define BU(i) bu[(i) * 32 + lane]
+#define BV(i) bv[(i) * 32 + lane]
+    const int64_t stride = (int64_t)gridDim.x * LWARPS * 32;
+    for (int64_t vox = ((int64_t)blockIdx.x * LWARPS + warp) * 32 + lane; vox < P.n_vox; vox += stride) {
+        const int v = krig_find_vol(P, vox, 2);
+        const KrigVol& V = P.vol[v];
+        const int r = V.r;
+        if (r > 1) continue;  // voxel of the warp-per-voxel kernel
+        const int64_t local = vox - V.vox_begin;
+        const int64_t plane = (int64_t)V.H * V.W;
+        const int z = (int)(local / plane);
+        const int64_t pix = local % plane;
+        const int y = (int)(pix / V.W), x = (int)(pix % V.W);
+        const int g = V.g, j = z / g, t = z % g;
+        const bool f64 = V.dtype == KRIG_F64;
+        if (t == 0) {  // known slice: copy through
+            const double val = in_value(P.in[v], V.dtype, V.scale, (int64_t)j * plane + pix);
+            if (f64) ((double*)P.out[v])[local] = val;
+            else ((float*)P.out[v])[local] = (float)val;
+            if (P.var[v]) P.var[v][local] = 0.0f;
+            continue;
+        }
+        LagDims d{r, g, 2 * r + 1, r + 1};
+        const double* gC = (const double*)(P.ws + V.lag_off);
+        const double* g0 = gC + d.nC();
+        const int lx = min(x, r), rx = min(V.W - 1 - x, r), ly = min(y, r), ry = min(V.H - 1 - y, r);
+        const int nx = lx + rx + 1, ny = ly + ry + 1, nxy = nx * ny;
+        const int K = 2 * nxy;
+        // system (lower triangle, row-major) and right-hand sides; point i is
+        // (slice i / nxy, dy = (i / nx) % ny - ly, dx = i % nx - lx)
+        for (int i = 0; i < K; ++i) {
+            const int si = i / nxy, dyi = (i / nx) % ny - ly, dxi = i % nx - lx;
+            for (int k = 0; k <= i; ++k) {
+                const int sk = k / nxy, dyk = (k / nx) % ny - ly, dxk = k % nx - lx;
+                LE(i * (i + 1) / 2 + k) = __ldg(gC + d.iC(si != sk, abs(dyi - dyk), abs(dxi - dxk)));
+            }
+            BU(i) = __ldg(g0 + d.i0(t, si, abs(dyi), abs(dxi)));
+            BV(i) = 1.0;
+        }
+        // LDL': column k of L below the diagonal replaces a_ik, 1/d_k replaces a_kk
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            const int kk = k * (k + 1) / 2;
+            const double dk = LE(kk + k);
+            if (!(dk > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double inv = 1.0 / dk;
+            LE(kk + k) = inv;
+            for (int i = k + 1; i < K; ++i) {
+                const int ii = i * (i + 1) / 2;
+                const double ti = LE(ii + k);  // unscaled a_ik
+                const double li = ti * inv;
+                LE(ii + k) = li;
+#pragma unroll 4
+                for (int jj = k + 1; jj < i; ++jj) LE(ii + jj) = fma(-ti, LE(jj * (jj + 1) / 2 + k), LE(ii + jj));
+                LE(ii + i) = fma(-ti, li, LE(ii + i));
+            }
+        }
+        double est, var;
+        if (ok) {
+            // L y = b (unit lower), then D z = y, then L' x = z, for u and v at once
+            for (int i = 1; i < K; ++i) {
+                const int ii = i * (i + 1) / 2;
+                double au = BU(i), av = BV(i);
+#pragma unroll 4
+                for (int k = 0; k < i; ++k) {
+                    const double l = LE(ii + k);
+                    au = fma(-l, BU(k), au);
+                    av = fma(-l, BV(k), av);
+                }
+                BU(i) = au;
+                BV(i) = av;
+            }
+            for (int i = 0; i < K; ++i) {
+                const double inv = LE(i * (i + 1) / 2 + i);
+                BU(i) *= inv;
+                BV(i) *= inv;
+            }
+            for (int i = K - 2; i >= 0; --i) {
+                double au = BU(i), av = BV(i);
+#pragma unroll 4
+                for (int k = i + 1; k < K; ++k) {
+                    const double l = LE(k * (k + 1) / 2 + i);
+                    au = fma(-l, BU(k), au);
+                    av = fma(-l, BV(k), av);
+                }
+                BU(i) = au;
+                BV(i) = av;
+            }
+            double su = 0.0, sv = 0.0;
+            for (int i = 0; i < K; ++i) {
+                su += BU(i);
+                sv += BV(i);
+            }
+            const double phi = (su - 1.0) / sv;
+            double wz = 0.0, wc = 0.0;
+            for (int i = 0; i < K; ++i) {
+                const int si = i / nxy, dyi = (i / nx) % ny - ly, dxi = i % nx - lx;
+                const double w = BU(i) - phi * BV(i);
+                const int64_t idx = (int64_t)(j + si) * plane + (int64_t)(y + dyi) * V.W + (x + dxi);
+                wz += w * in_value(P.in[v], V.dtype, V.scale, idx);
+                wc += w * __ldg(g0 + d.i0(t, si, abs(dyi), abs(dxi)));
+            }
+            est = wz;
+            var = gC[0] - wc - phi;
+        } else {
+            est = var = __longlong_as_double(0x7ff8000000000000LL);
+            krig_set_status(P.status, KRIG_DEV_SINGULAR);
+        }
+        if (f64) ((double*)P.out[v])[local] = est;
+        else ((float*)P.out[v])[local] = (float)est;
+        if (P.var[v]) P.var[v][local] = (float)var;
+    }
+#undef LE
+#undef BU
+#undef BV
+}
+
 template <typename TF, int RMAX>
-static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st)
+static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st, int rmin)
 {
     const size_t smem = 8 * VoxSmemMax<TF, RMAX>::bytes;
     if (smem > 48 * 1024) {
@@ -182,7 +327,20 @@ static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st)
     int64_t need = (L.n_vox + 7) / 8;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_voxel<TF, RMAX><<<(unsigned)grid, 256, smem, st>>>(L);
+    k_voxel<TF, RMAX><<<(unsigned)grid, 256, smem, st>>>(L, rmin);
+    return (int)cudaGetLastError();
+}
+
+static int launch_voxel_lane(const KrigLaunch& L, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_voxel_lane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LSMEM);
+    if (e != cudaSuccess) return (int)e;
+    const int sms = krig_device_sm_count();
+    int64_t grid = sms > 0 ? sms : 1;
+    const int64_t need = (L.n_vox + LWARPS * 32 - 1) / (LWARPS * 32);
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_voxel_lane<<<(unsigned)grid, LWARPS * 32, LSMEM, st>>>(L);
     return (int)cudaGetLastError();
 }
 
@@ -196,7 +354,17 @@ int krig_launch_voxel(const KrigLaunch& L, int form, void* stream)
     int rmax = 0;
     for (int v = 0; v < L.n_vols; ++v) rmax = L.vol[v].r > rmax ? L.vol[v].r : rmax;
     const bool fp64 = form == KRIG_FORM_P64;
-    if (rmax == 0) return fp64 ? launch_voxel_t<double, 0>(L, st) : launch_voxel_t<float, 0>(L, st);
-    if (rmax == 1) return fp64 ? launch_voxel_t<double, 1>(L, st) : launch_voxel_t<float, 1>(L, st);
-    return fp64 ? launch_voxel_t<double, 2>(L, st) : launch_voxel_t<float, 2>(L, st);
+    if (fp64) {
+        // voxels of volumes with r <= 1: one per lane; r = 2: one per warp
+        int rmin = 0;
+        for (int v = 0; v < L.n_vols; ++v) rmin = (v == 0 || L.vol[v].r < rmin) ? L.vol[v].r : rmin;
+        if (rmin <= 1) {
+            const int rc = launch_voxel_lane(L, st);
+            if (rc) return rc;
+        }
+        return rmax == 2 ? launch_voxel_t<double, 2>(L, st, 2) : 0;
+    }
+    if (rmax == 0) return launch_voxel_t<float, 0>(L, st, 0);
+    if (rmax == 1) return launch_voxel_t<float, 1>(L, st, 0);
+    return launch_voxel_t<float, 2>(L, st, 0);
 }
