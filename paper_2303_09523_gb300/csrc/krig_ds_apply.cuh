@@ -446,86 +446,115 @@ template <typename TI> struct DsLayout {
     }
 };
 
+// Per-item constants of a consumer thread, taken out of the kernel parameters
+// once per item: inside the slice loop the barrier waits (asm with a memory
+// clobber) would otherwise force every parameter read to be repeated.
+template <typename TI>
+struct DsCtx {
+    typename DsTypes<TI>::TO* out;  // output at this thread's first pixel, slice 0
+    float* var;                     // variance likewise, or null
+    const float* vt;                // variance row of the interior class
+    int64_t plane;                  // H * W
+    int g, jlast;                   // Z factor; gap index whose upper slice is the last one
+    float scale;
+    int nvalid, plo, phi;           // valid pixels of the four; interior ones [plo, phi)
+    bool mine, vec_out, inner, full;
+};
+
+template <typename TI, int R>
+__device__ __forceinline__ DsCtx<TI> ds_ctx(const KrigLaunch& P, const DsItem& d, int lrow, int lcol, bool dry)
+{
+    typedef typename DsTypes<TI>::TO TO;
+    const KrigVol& V = P.vol[d.v];
+    DsCtx<TI> c;
+    const int H = V.H, W = V.W;
+    const int y = d.y0 + lrow, xb = d.x0 + lcol;
+    c.plane = (int64_t)H * W;
+    c.g = V.g;
+    c.jlast = V.n - 2;
+    c.scale = V.scale;
+    c.nvalid = min(KRIG_PX, W - xb);
+    c.mine = y < H && c.nvalid > 0;
+    c.vec_out = (W % KRIG_PX == 0) && c.nvalid == KRIG_PX;
+    const int64_t pix = c.mine ? (int64_t)y * W + xb : 0;
+    c.out = (TO*)P.out[d.v] + pix;
+    c.var = (dry || !P.var[d.v]) ? nullptr : P.var[d.v] + pix;
+    c.vt = (const float*)(P.ws + V.vtab_off) + (int64_t)max(V.cint, 0) * KRIG_TSLOTS;
+    // interior pixels of the four: rows y in [R, H-1-R], x in [R, W-1-R]
+    c.plo = max(0, R - xb);
+    c.phi = min(c.nvalid, W - R - xb);
+    c.inner = c.mine && V.cint >= 0 && y >= R && y <= H - 1 - R && c.plo < c.phi;
+    c.full = c.vec_out && c.plo == 0 && c.phi == KRIG_PX;
+    return c;
+}
+
 // One gap of one item for the consumer warps: passthrough of known slice j
 // for every pixel, and the g-1 interpolated slices (with variance) for the
 // interior pixels, through the orbit sums.  Frame pixels (within r of the
-// border) are written by the frame units instead.
+// border) are written by the frame warp instead.
 template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_gap(const KrigLaunch& P, const KrigVol& V, int v, const DsItem& d, int j,
-                                       const TI* lo, const TI* hi, int lrow, int lcol,
+__device__ __forceinline__ void ds_gap(const DsCtx<TI>& c, int j, const TI* lo, const TI* hi, int lrow, int lcol,
                                        const typename DsTypes<TI>::TC* ow, bool dry)
 {
     typedef typename DsTypes<TI>::TC TC;
     typedef typename DsTypes<TI>::TO TO;
     constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    const int H = V.H, W = V.W, g = V.g;
-    const int64_t plane = (int64_t)H * W;
-    const int y = d.y0 + lrow, xb = d.x0 + lcol;
-    const int nvalid = min(KRIG_PX, W - xb);
-    if (y >= H || nvalid <= 0) return;
-    const bool vec_out = (W % KRIG_PX == 0) && nvalid == KRIG_PX;
-    TO* out = (TO*)P.out[v];
-    float* var = dry ? nullptr : P.var[v];
-    const int64_t pix = (int64_t)y * W + xb;
+    if (!c.mine) return;
+    const int64_t jg = (int64_t)j * c.g * c.plane;
     {   // known slice j -> output slice j*g, bit-exact
         TO kv[4];
         const TI* cptr = lo + (lrow + R) * RP + PAD + lcol;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(cptr[p], V.scale);
-        if (!dry) st4<TO>(out + (int64_t)j * g * plane + pix, kv, vec_out, nvalid);
-        if (var) {
+        for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(cptr[p], c.scale);
+        if (!dry) st4<TO>(c.out + jg, kv, c.vec_out, c.nvalid);
+        if (c.var) {
             const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-            st4<float>(var + (int64_t)j * g * plane + pix, z4, vec_out, nvalid);
+            st4<float>(c.var + jg, z4, c.vec_out, c.nvalid);
         }
-        if (j == V.n - 2) {  // the volume's last known slice
+        if (j == c.jlast) {  // the volume's last known slice
             const TI* ch_ = hi + (lrow + R) * RP + PAD + lcol;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(ch_[p], V.scale);
-            if (!dry) st4<TO>(out + (int64_t)(j + 1) * g * plane + pix, kv, vec_out, nvalid);
-            if (var) {
+            for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(ch_[p], c.scale);
+            const int64_t jg1 = jg + (int64_t)c.g * c.plane;
+            if (!dry) st4<TO>(c.out + jg1, kv, c.vec_out, c.nvalid);
+            if (c.var) {
                 const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-                st4<float>(var + (int64_t)(j + 1) * g * plane + pix, z4, vec_out, nvalid);
+                st4<float>(c.var + jg1, z4, c.vec_out, c.nvalid);
             }
         }
     }
     if constexpr (GM1 == 0) {
         return;
     } else {
-        if (V.cint < 0 || y < R || y > H - 1 - R) return;  // no interior pixel in this row
-        // interior pixels of the four: x in [R, W-1-R]
-        const int plo = max(0, R - xb), phi = min(nvalid, W - R - xb);  // [plo, phi)
-        if (plo >= phi) return;
+        if (!c.inner) return;  // no interior pixel among the four
         TC acc[KRIG_PX][GM1];
 #pragma unroll
         for (int p = 0; p < KRIG_PX; ++p)
 #pragma unroll
             for (int t = 0; t < GM1; ++t) acc[p][t] = TC(0);
         ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, ow);
-        const bool full = vec_out && plo == 0 && phi == KRIG_PX;
-        const float vint = 0.0f;
-        const float* vt = (const float*)(P.ws + V.vtab_off) + (int64_t)V.cint * KRIG_TSLOTS;
-        (void)vint;
 #pragma unroll
         for (int t = 0; t < GM1; ++t) {
             TO o[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][t];
-            TO* dst = out + ((int64_t)j * g + t + 1) * plane + pix;
-            float* vdst = var ? var + ((int64_t)j * g + t + 1) * plane + pix : nullptr;
+            const int64_t off = jg + (int64_t)(t + 1) * c.plane;
             if (dry) {
                 // warm-up pass: no stores
-            } else if (full) {
-                st4<TO>(dst, o, true, 4);
-                if (vdst) {
-                    const float vv = vt[t];
+            } else if (c.full) {
+                st4<TO>(c.out + off, o, true, 4);
+                if (c.var) {
+                    const float vv = c.vt[t];
                     const float v4[4] = {vv, vv, vv, vv};
-                    st4<float>(vdst, v4, true, 4);
+                    st4<float>(c.var + off, v4, true, 4);
                 }
             } else {
-                for (int p = plo; p < phi; ++p) {
-                    dst[p] = o[p];
-                    if (vdst) vdst[p] = vt[t];
-                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    if (p >= c.plo && p < c.phi) {
+                        c.out[off + p] = o[p];
+                        if (c.var) c.var[off + p] = c.vt[t];
+                    }
             }
         }
     }
@@ -635,19 +664,19 @@ __device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsIte
 {
     constexpr int DS_STAGES = DsStages<TI>::S;
     typedef typename DsTypes<TI>::TC TC;
-    const KrigVol& V = P.vol[d.v];
     // interior orbit weights of the item's volume
     const TC* ow = (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS);  // shared memory
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
+    const DsCtx<TI> ctx = ds_ctx<TI, R>(P, d, lrow, lcol, dry);
     const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
     bool ok = mbar_wait(&sh.full[q % DS_STAGES], (q / DS_STAGES) & 1, DS_WAIT_LIMIT);
     for (int m = 0; m + 1 < nsl && ok; ++m) {
         const int ql = q + m, qh = q + m + 1;
         ok = mbar_wait(&sh.full[qh % DS_STAGES], (qh / DS_STAGES) & 1, DS_WAIT_LIMIT);
         if (!ok) break;
-        ds_gap<TI, R, GM1>(P, V, d.v, d, d.c0 + m, slots + (ql % DS_STAGES) * stride,
-                           slots + (qh % DS_STAGES) * stride, lrow, lcol, ow, dry);
+        ds_gap<TI, R, GM1>(ctx, d.c0 + m, slots + (ql % DS_STAGES) * stride, slots + (qh % DS_STAGES) * stride, lrow,
+                           lcol, ow, dry);
         __syncwarp();
         if (lane == 0 && !dry) mbar_arrive(&sh.empty[ql % DS_STAGES]);
     }
