@@ -240,46 +240,24 @@ __device__ __forceinline__ void ds_plain_fill(TI* slot, uint64_t* bar, const TI*
 // Accumulation
 // ---------------------------------------------------------------------------
 
-// General path: full weight row per pixel class, taps from both slices.
-template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_accum_general(typename DsTypes<TI>::TC (&acc)[KRIG_PX][GM1 > 0 ? GM1 : 1],
-                                                 const TI* lo, const TI* hi, int lrow, int lcol,
-                                                 const typename DsTypes<TI>::TC* wrow, unsigned mask)
+// Two floats as one 64-bit register pair and back (operands of the packed
+// f32x2 instructions).
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
 {
-    typedef typename DsTypes<TI>::TC TC;
-    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    constexpr int N2R = 2 * R + 1;
-#pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
-        const TI* slot = s == 0 ? lo : hi;
-#pragma unroll 1
-        for (int dy = -R; dy <= R; ++dy) {
-            const TI* rowp = slot + (lrow + R + dy) * RP + PAD + lcol;
-            TC a[4], b[4], c[4];
-            ld4(rowp - 4, a);
-            ld4(rowp, b);
-            ld4(rowp + 4, c);
-            const TC vals[12] = {a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], c[0], c[1], c[2], c[3]};
-#pragma unroll
-            for (int dx = -R; dx <= R; ++dx) {
-                TC w[8];
-                ldgw8(wrow + ((s * N2R + (dy + R)) * N2R + (dx + R)) * KRIG_TSLOTS, w);
-#pragma unroll
-                for (int p = 0; p < KRIG_PX; ++p) {
-                    if (!((mask >> p) & 1u)) continue;
-                    const TC x = vals[4 + p + dx];
-#pragma unroll
-                    for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], x, acc[p][t]);
-                }
-            }
-        }
-    }
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
+__device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+template <int GM1> struct DsGP { static constexpr int N = GM1 > 0 ? GM1 : 1; };  // accumulators per pixel
 
 // Interior path: orbit sums of each slice times the interior orbit weights.
 // ow: shared [2][KRIG_NORB][8] orbit weights.
 template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc)[KRIG_PX][GM1 > 0 ? GM1 : 1],
+__device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc)[KRIG_PX][DsGP<GM1>::N],
                                                   const TI* lo, const TI* hi, int lrow, int lcol,
                                                   const typename DsTypes<TI>::TC* ow)
 {
@@ -357,10 +335,25 @@ __device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc
         for (int o = 0; o < NO; ++o) {
             TC w[8];
             ldw8(ow + (s * KRIG_NORB + o) * KRIG_TSLOTS, w);
+            if constexpr (sizeof(TC) == 4) {
+                // two targets per packed FMA (fma.rn.f32x2: each half rounds as fmaf)
 #pragma unroll
-            for (int p = 0; p < KRIG_PX; ++p)
+                for (int p = 0; p < KRIG_PX; ++p) {
+                    const unsigned long long ob = pk2(orb[p][o], orb[p][o]);
 #pragma unroll
-                for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], orb[p][o], acc[p][t]);
+                    for (int t = 0; t + 1 < GM1; t += 2) {
+                        unsigned long long a2 = pk2(acc[p][t], acc[p][t + 1]);
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(pk2(w[t], w[t + 1])), "l"(ob));
+                        upk2(a2, acc[p][t], acc[p][t + 1]);
+                    }
+                    if (GM1 & 1) acc[p][GM1 - 1] = fmaf(w[GM1 - 1], orb[p][o], acc[p][GM1 - 1]);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < KRIG_PX; ++p)
+#pragma unroll
+                    for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], orb[p][o], acc[p][t]);
+            }
         }
     }
 }
@@ -527,11 +520,11 @@ __device__ __forceinline__ void ds_gap(const DsCtx<TI>& c, int j, const TI* lo, 
         return;
     } else {
         if (!c.inner) return;  // no interior pixel among the four
-        TC acc[KRIG_PX][GM1];
+        TC acc[KRIG_PX][DsGP<GM1>::N];
 #pragma unroll
         for (int p = 0; p < KRIG_PX; ++p)
 #pragma unroll
-            for (int t = 0; t < GM1; ++t) acc[p][t] = TC(0);
+            for (int t = 0; t < DsGP<GM1>::N; ++t) acc[p][t] = TC(0);
         ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, ow);
 #pragma unroll
         for (int t = 0; t < GM1; ++t) {
