@@ -526,28 +526,34 @@ __device__ __forceinline__ void ds_gap(const DsCtx<TI>& c, int j, const TI* lo, 
 #pragma unroll
             for (int t = 0; t < DsGP<GM1>::N; ++t) acc[p][t] = TC(0);
         ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, ow);
+        if (dry) return;  // warm-up pass: no stores
+        // the g-1 output slices of the gap, one branch for the whole set
+        if (c.full) {
 #pragma unroll
-        for (int t = 0; t < GM1; ++t) {
-            TO o[4];
+            for (int t = 0; t < GM1; ++t) {
+                TO o[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][t];
-            const int64_t off = jg + (int64_t)(t + 1) * c.plane;
-            if (dry) {
-                // warm-up pass: no stores
-            } else if (c.full) {
-                st4<TO>(c.out + off, o, true, 4);
-                if (c.var) {
-                    const float vv = c.vt[t];
-                    const float v4[4] = {vv, vv, vv, vv};
-                    st4<float>(c.var + off, v4, true, 4);
-                }
-            } else {
+                for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][t];
+                st4<TO>(c.out + jg + (int64_t)(t + 1) * c.plane, o, true, 4);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < GM1; ++t)
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
-                    if (p >= c.plo && p < c.phi) {
-                        c.out[off + p] = o[p];
-                        if (c.var) c.var[off + p] = c.vt[t];
-                    }
+                    if (p >= c.plo && p < c.phi) c.out[jg + (int64_t)(t + 1) * c.plane + p] = (TO)acc[p][t];
+        }
+        if (c.var) {
+#pragma unroll
+            for (int t = 0; t < GM1; ++t) {
+                const float vv = c.vt[t];
+                const int64_t off = jg + (int64_t)(t + 1) * c.plane;
+                if (c.full) {
+                    const float v4[4] = {vv, vv, vv, vv};
+                    st4<float>(c.var + off, v4, true, 4);
+                } else {
+                    for (int p = c.plo; p < c.phi; ++p) c.var[off + p] = vv;
+                }
             }
         }
     }
