@@ -411,6 +411,70 @@ __device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype
     return d.c0 < d.c1;
 }
 
+// The fields of one volume that the consumer loop needs, one copy per warp in
+// shared memory: read from the kernel parameters once per volume instead of
+// once per item (parameter reads that miss the constant cache take a round
+// trip to L2), without holding registers across the loop.
+template <typename TI>
+struct DsVolR {
+    int v, match;                 // volume index; its items are of this kernel's type and shape
+    int item_begin, tiles_x, tiles, chunks, chunk, gq, grm;
+    uint64_t mt, mc, mx;          // multiply-high divisors: tiles, chunks, tiles_x
+    int H, W, g, jlast, cint;
+    float scale;
+    typename DsTypes<TI>::TO* out;
+    float* var;
+    const float* vt;
+};
+
+template <typename TI>
+__device__ __forceinline__ DsVolR<TI> ds_volr(const KrigLaunch& P, int v, int dtype, int shape)
+{
+    typedef typename DsTypes<TI>::TO TO;
+    const KrigVol& V = P.vol[v];
+    DsVolR<TI> R;
+    R.v = v;
+    R.match = V.dtype == dtype && ds_shape(V) == shape;
+    R.item_begin = (int)V.item_begin;
+    R.tiles_x = V.tiles_x;
+    R.tiles = V.tiles_x * V.tiles_y;
+    R.chunks = V.chunks;
+    R.chunk = V.chunk;
+    R.gq = V.gq;
+    R.grm = V.grm;
+    R.mt = V.mdiv_tiles;
+    R.mc = V.mdiv_chunks;
+    R.mx = V.mdiv_tx;
+    R.H = V.H;
+    R.W = V.W;
+    R.g = V.g;
+    R.jlast = V.n - 2;
+    R.cint = V.cint;
+    R.scale = V.scale;
+    R.out = (TO*)P.out[v];
+    R.var = P.var[v];
+    R.vt = (const float*)(P.ws + V.vtab_off) + (int64_t)max(V.cint, 0) * KRIG_TSLOTS;
+    return R;
+}
+
+// ds_decode on the register copy.
+template <typename TI>
+__device__ __forceinline__ bool ds_decode_r(const DsVolR<TI>& R, int it, DsItem& d)
+{
+    const uint32_t local = (uint32_t)(it - R.item_begin);
+    const uint32_t rest = krig_udiv(local, R.mt), tile = local - rest * (uint32_t)R.tiles;
+    const uint32_t bb = krig_udiv(rest, R.mc), ch = rest - bb * (uint32_t)R.chunks;
+    const uint32_t ty = krig_udiv(tile, R.mx), tx = tile - ty * (uint32_t)R.tiles_x;
+    const int b = (int)bb;
+    const int a0 = b * R.gq + min(b, R.grm), a1 = (b + 1) * R.gq + min(b + 1, R.grm);
+    d.v = R.v;
+    d.c0 = a0 + (int)ch * R.chunk;
+    d.c1 = min(d.c0 + R.chunk, a1);
+    d.x0 = (int)tx * KRIG_TX;
+    d.y0 = (int)ty * KRIG_TY;
+    return d.c0 < d.c1;
+}
+
 struct DsShared {
     void* ow;          // interior orbit weights of every volume, [v][2][NORB][8]
     uint64_t* full;
@@ -428,9 +492,11 @@ template <typename TI> struct DsLayout {
     static constexpr int S = DsStages<TI>::S;
     static constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;  // slot stride, elements
     static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
-    static constexpr size_t bytes = bar_off + (2 * S + 2) * sizeof(uint64_t) +
-                                    (size_t)KRIG_MAX_VOLUMES * 2 * KRIG_NORB * KRIG_TSLOTS *
-                                        sizeof(typename DsTypes<TI>::TC);
+    static constexpr size_t ow_bytes =
+        (size_t)KRIG_MAX_VOLUMES * 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(typename DsTypes<TI>::TC);
+    static constexpr size_t vr_off = (bar_off + (2 * S + 2) * sizeof(uint64_t) + ow_bytes + 15) / 16 * 16;
+    static constexpr size_t bytes = vr_off + DS_CONSUMERS * sizeof(DsVolR<TI>);
+    __device__ static __forceinline__ DsVolR<TI>* volr(int warp) { return (DsVolR<TI>*)(ds_smem + vr_off) + warp; }
     __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
     __device__ static __forceinline__ DsShared shared()
     {
@@ -455,24 +521,22 @@ struct DsCtx {
 };
 
 template <typename TI, int R>
-__device__ __forceinline__ DsCtx<TI> ds_ctx(const KrigLaunch& P, const DsItem& d, int lrow, int lcol, bool dry)
+__device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolR<TI>& V, const DsItem& d, int lrow, int lcol, bool dry)
 {
-    typedef typename DsTypes<TI>::TO TO;
-    const KrigVol& V = P.vol[d.v];
     DsCtx<TI> c;
     const int H = V.H, W = V.W;
     const int y = d.y0 + lrow, xb = d.x0 + lcol;
     c.plane = (int64_t)H * W;
     c.g = V.g;
-    c.jlast = V.n - 2;
+    c.jlast = V.jlast;
     c.scale = V.scale;
     c.nvalid = min(KRIG_PX, W - xb);
     c.mine = y < H && c.nvalid > 0;
     c.vec_out = (W % KRIG_PX == 0) && c.nvalid == KRIG_PX;
     const int64_t pix = c.mine ? (int64_t)y * W + xb : 0;
-    c.out = (TO*)P.out[d.v] + pix;
-    c.var = (dry || !P.var[d.v]) ? nullptr : P.var[d.v] + pix;
-    c.vt = (const float*)(P.ws + V.vtab_off) + (int64_t)max(V.cint, 0) * KRIG_TSLOTS;
+    c.out = V.out + pix;
+    c.var = (dry || !V.var) ? nullptr : V.var + pix;
+    c.vt = V.vt;
     // interior pixels of the four: rows y in [R, H-1-R], x in [R, W-1-R]
     c.plo = max(0, R - xb);
     c.phi = min(c.nvalid, W - R - xb);
@@ -658,8 +722,8 @@ __device__ __forceinline__ void ds_frame_dispatch(const KrigLaunch& P, int v, in
 }
 
 template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsItem& d, int q, TI* slots, int stride,
-                                                const DsShared& sh, int warp, int lane, bool dry)
+__device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsVolR<TI>& VR, const DsItem& d, int q,
+                                                TI* slots, int stride, const DsShared& sh, int warp, int lane, bool dry)
 {
     constexpr int DS_STAGES = DsStages<TI>::S;
     typedef typename DsTypes<TI>::TC TC;
@@ -667,7 +731,7 @@ __device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsIte
     const TC* ow = (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS);  // shared memory
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
-    const DsCtx<TI> ctx = ds_ctx<TI, R>(P, d, lrow, lcol, dry);
+    const DsCtx<TI> ctx = ds_ctx<TI, R>(VR, d, lrow, lcol, dry);
     const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
     bool ok = mbar_wait(&sh.full[q % DS_STAGES], (q / DS_STAGES) & 1, DS_WAIT_LIMIT);
     for (int m = 0; m + 1 < nsl && ok; ++m) {
@@ -703,11 +767,23 @@ __device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, i
 {
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     const DsShared sh = DsLayout<TI>::shared();
-    for (int it = blockIdx.x; it < (int)P.n_items; it += gridDim.x) {
+    const int n_vols = P.n_vols, n_items = (int)P.n_items;
+    DsVolR<TI>& VR = *DsLayout<TI>::volr(warp);
+    if (lane == 0) VR = ds_volr<TI>(P, 0, dtype, R * 8 + GM1);
+    __syncwarp();
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        int v = 0;
+        for (int u = 1; u < n_vols; ++u)
+            if (P.vol[u].item_begin <= it) v = u;
+        if (v != VR.v) {
+            __syncwarp();
+            if (lane == 0) VR = ds_volr<TI>(P, v, dtype, R * 8 + GM1);
+            __syncwarp();
+        }
         DsItem d;
-        if (!ds_decode(P, it, dtype, R * 8 + GM1, d)) continue;
+        if (!VR.match || !ds_decode_r(VR, it, d)) continue;
         if (*(volatile int*)sh.abort) break;
-        ds_consume_item<TI, R, GM1>(P, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane, dry);
+        ds_consume_item<TI, R, GM1>(P, VR, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane, dry);
         if (dry) break;
         q += d.c1 - d.c0 + 1;
     }
