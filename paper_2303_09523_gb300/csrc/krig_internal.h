@@ -74,6 +74,7 @@ struct KrigVol {
     int64_t lbar_off;         // sum r S_k per class tap, same layout, double, KRIG_LOO_REP copies
     int64_t res_off;          // residuals (n-2) x H x W float
     int64_t lacc_off;         // loss accumulators, KRIG_LOO_REP doubles
+    int64_t lorb_off;         // interior class: sum r * (orbit sum of both slices), [KRIG_LOO_REP][NORB] doubles
 };
 
 struct KrigLaunch {
@@ -240,6 +241,8 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     *off = up(*off + (int64_t)(V.n - 2) * V.H * V.W * 4);
     V.lacc_off = *off;
     *off = up(*off + KRIG_LOO_REP * 8);
+    V.lorb_off = *off;
+    *off = up(*off + KRIG_LOO_REP * KRIG_NORB * 8);
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times

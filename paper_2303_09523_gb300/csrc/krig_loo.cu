@@ -90,15 +90,19 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
             const int ax = e % n2r, ay = (e / n2r) % n2r, s = e / (n2r * n2r);
             h2 = (double)(ax * ax + ay * ay) + (double)(s * g2) * (double)(s * g2);
             gC[e] = krig_cov(vg, h2);
-            krig_cov_grad(vg, h2, dd);
-            for (int p = 0; p < 3; ++p) dC[p][e] = dd[p];
+            if (mode == 1) {  // covariance derivatives: the adjoint pass only
+                krig_cov_grad(vg, h2, dd);
+                for (int p = 0; p < 3; ++p) dC[p][e] = dd[p];
+            }
         } else {
             const int f = e - nC;
             const int ax = f % nr, ay = (f / nr) % nr;
             h2 = (double)(ax * ax + ay * ay) + (double)V.g * (double)V.g;  // dz = g both sides
             g0[f] = krig_cov(vg, h2);
-            krig_cov_grad(vg, h2, dd);
-            for (int p = 0; p < 3; ++p) d0[p][f] = dd[p];
+            if (mode == 1) {
+                krig_cov_grad(vg, h2, dd);
+                for (int p = 0; p < 3; ++p) d0[p][f] = dd[p];
+            }
         }
     }
     __syncthreads();
@@ -128,6 +132,23 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
             for (int s = 0; s < 2; ++s) {
                 const int full = (s * n2r + (dy + r)) * n2r + (dx + r);
                 for (int c = 0; c < KRIG_LOO_REP; ++c) sum += lbar[c * lrep + full];
+            }
+            if (local == V.cint) {
+                // interior class: the residual kernel kept only orbit sums (both
+                // slices); dL/dtheta depends on wbar only through them (the class
+                // system and its symmetric right-hand sides are D4-invariant), so
+                // each orbit's total is spread evenly over its taps
+                const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy)), o = a * (a + 1) / 2 + b;
+                int cnt = 0;
+                for (int qy = -r; qy <= r; ++qy)
+                    for (int qx = -r; qx <= r; ++qx) {
+                        const int qa = max(abs(qx), abs(qy)), qb = min(abs(qx), abs(qy));
+                        cnt += (qa * (qa + 1) / 2 + qb) == o;
+                    }
+                const double* lorb = (const double*)(P.ws + V.lorb_off);
+                double g = 0.0;
+                for (int c = 0; c < KRIG_LOO_REP; ++c) g += lorb[c * KRIG_NORB + o];
+                sum += g / cnt;
             }
             S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
         }
@@ -226,6 +247,66 @@ __device__ __forceinline__ float loo_load(const void* in, int dtype, float scale
     return (float)((const double*)in)[idx];
 }
 
+// D4 orbit sums of a + b (two tiles with the residual-kernel layout) around
+// the four pixels of a thread: the LOO interior class is D4-symmetric and has
+// the same weights in both slices, so its stencil is sum_o w_o * orbit sum.
+template <int R> struct LooNO { static constexpr int N = R == 0 ? 1 : (R == 1 ? 3 : 6); };
+
+template <int R>
+__device__ __forceinline__ void loo_orbits(const float* a, const float* b, int lrow, int lcol,
+                                           float (&o)[4][LooNO<R>::N])
+{
+    constexpr int NC = 4 + 2 * R;
+    float F[2 * R + 1][NC];
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const int idx = (lrow + R + dy) * LOO_RP + LOO_PAD + lcol + k - R;
+            F[dy + R][k] = a[idx] + b[idx];
+        }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int m = R + p;
+        o[p][0] = F[R][m];
+        if (R >= 1) {
+            o[p][1] = (F[R][m - 1] + F[R][m + 1]) + (F[R - 1][m] + F[R + 1][m]);
+            o[p][2] = (F[R - 1][m - 1] + F[R - 1][m + 1]) + (F[R + 1][m - 1] + F[R + 1][m + 1]);
+        }
+        if (R >= 2) {
+            o[p][3] = (F[R][m - 2] + F[R][m + 2]) + (F[R - 2][m] + F[R + 2][m]);
+            o[p][4] = ((F[R - 1][m - 2] + F[R - 1][m + 2]) + (F[R + 1][m - 2] + F[R + 1][m + 2])) +
+                      ((F[R - 2][m - 1] + F[R - 2][m + 1]) + (F[R + 2][m - 1] + F[R + 2][m + 1]));
+            o[p][5] = (F[R - 2][m - 2] + F[R - 2][m + 2]) + (F[R + 2][m - 2] + F[R + 2][m + 2]);
+        }
+    }
+}
+
+// Orbit index of an in-plane offset and the interior class's weight per orbit
+// (the mean over the orbit's taps of one slice; both slices are equal).
+__device__ __forceinline__ int loo_orbit(int dx, int dy)
+{
+    const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy));
+    return a * (a + 1) / 2 + b;
+}
+
+template <int R>
+__device__ __forceinline__ void loo_orbit_weights(const float* wrow, float* wo, int tid)
+{
+    constexpr int N2R = 2 * R + 1;
+    if (tid < LooNO<R>::N) {
+        float sum = 0.f;
+        int cnt = 0;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx)
+                if (loo_orbit(dx, dy) == tid) {
+                    sum += wrow[(dy + R) * N2R + (dx + R)];
+                    ++cnt;
+                }
+        wo[tid] = sum / (float)cnt;
+    }
+}
+
 template <int R>
 __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int y0, int mode, float* sm)
 {
@@ -240,6 +321,9 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     float* sg = ce + LOO_TY * LOO_TX;                // [ncls][NTAP] tap sums (mode 1)
     double* sl = (double*)(sg + 32 * NTAP + 2);      // loss partials of the warps (8)
     float* wsm = (float*)(sl + 8);                   // [ncls][NTAP] LOO weights
+    float* wo = wsm + 25 * NTAP;                     // interior weight per orbit
+    float* sgo = wo + 8;                             // interior sum r * orbit sum (mode 1)
+    constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncls = V.ncx * V.ncy;
     for (int e = tid; e < ROWS * LOO_RP; e += 256) {
@@ -262,36 +346,46 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     {
         const float* lwg = (const float*)(P.ws + V.lw_off);
         for (int e = tid; e < ncls * NTAP; e += 256) wsm[e] = lwg[e];
+        if (V.cint >= 0) loo_orbit_weights<R>(lwg + (int64_t)V.cint * NTAP, wo, tid);
+        if (tid < 8) sgo[tid] = 0.f;
     }
     __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int y = y0 + lrow;
     const float* lw = wsm;
-    float gi[NTAP];
+    float gio[NO];
 #pragma unroll
-    for (int k = 0; k < NTAP; ++k) gi[k] = 0.f;
+    for (int o = 0; o < NO; ++o) gio[o] = 0.f;
     double loss = 0.0;
     if (y < H) {
+        // interior pixels: orbit sums of the two slices, one FMA per orbit
+        const bool row_in = V.cint >= 0 && y >= R && y <= H - 1 - R;
+        float orb[4][NO];
+        if (row_in) loo_orbits<R>(lo, hi, lrow, lcol, orb);
         const int cy = V.ymap[krig_slot(y, H, R)];
+#pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int x = x0 + lcol + p;
             if (x >= W) break;
             const int c = cy * V.ncx + V.xmap[krig_slot(x, W, R)];
-            const float* wr = lw + (int64_t)c * NTAP;
+            const bool inner = row_in && c == V.cint;
             float pred = 0.f;
-            float taps[NTAP];
+            if (inner) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
+                for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
+            } else {
+                const float* wr = lw + (int64_t)c * NTAP;
 #pragma unroll
-                for (int dy = -R; dy <= R; ++dy)
+                for (int s = 0; s < 2; ++s)
 #pragma unroll
-                    for (int dx = -R; dx <= R; ++dx) {
-                        const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
-                        const float z = (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx];
-                        taps[k] = z;
-                        pred = fmaf(wr[k], z, pred);
-                    }
+                    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                        for (int dx = -R; dx <= R; ++dx) {
+                            const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
+                            pred = fmaf(wr[k], (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx], pred);
+                        }
+            }
             const float res = pred - ce[lrow * LOO_TX + lcol + p];
             loss += (double)res * (double)res;
             const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x;
@@ -299,12 +393,20 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
                 if (P.pred[v]) P.pred[v][oidx] = pred;
             } else {
                 ((float*)(P.ws + V.res_off))[oidx] = res;
-                if (c == V.cint) {
+                if (inner) {
 #pragma unroll
-                    for (int k = 0; k < NTAP; ++k) gi[k] = fmaf(res, taps[k], gi[k]);
+                    for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < NTAP; ++k) atomicAdd(&sg[c * NTAP + k], res * taps[k]);
+                    for (int s = 0; s < 2; ++s)
+#pragma unroll
+                        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                            for (int dx = -R; dx <= R; ++dx) {
+                                const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
+                                const float z = (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx];
+                                atomicAdd(&sg[c * NTAP + k], res * z);
+                            }
                 }
             }
         }
@@ -314,10 +416,10 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     if (lane == 0) sl[warp] = loss;
     if (mode == 1 && V.cint >= 0) {
 #pragma unroll
-        for (int k = 0; k < NTAP; ++k) {
-            float t = gi[k];
-            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) atomicAdd(&sg[V.cint * NTAP + k], t);
+        for (int o = 0; o < NO; ++o) {
+            float t = gio[o];
+            for (int k = 16; k; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+            if (lane == 0) atomicAdd(&sgo[o], t);
         }
     }
     __syncthreads();
@@ -331,6 +433,8 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
         double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * NTAP;
         for (int e = tid; e < ncls * NTAP; e += 256)
             if (sg[e] != 0.f) atomicAdd(lbar + e, (double)sg[e]);
+        if (V.cint >= 0 && tid < NO && sgo[tid] != 0.f)
+            atomicAdd((double*)(P.ws + V.lorb_off) + rep * KRIG_NORB + tid, (double)sgo[tid]);
     }
 }
 
@@ -368,6 +472,8 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     float* rup = sm;                   // r_{m+1}: predictions for which S_m is the lower slice
     float* rdn = sm + ROWS * LOO_RP;   // r_{m-1}: predictions for which S_m is the upper slice
     float* wsm = rdn + ROWS * LOO_RP;  // [ncls][NTAP] LOO weights
+    float* wo = wsm + 25 * NTAP;       // interior weight per orbit
+    constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool has_up = m + 1 <= n - 2, has_dn = m - 1 >= 1;
     for (int e = tid; e < ROWS * LOO_RP; e += 256) {
@@ -384,6 +490,7 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     {
         const float* lwg = (const float*)(P.ws + V.lw_off);
         for (int e = tid; e < V.ncx * V.ncy * NTAP; e += 256) wsm[e] = lwg[e];
+        if (V.cint >= 0) loo_orbit_weights<R>(lwg + (int64_t)V.cint * NTAP, wo, tid);
     }
     __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
@@ -393,10 +500,20 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     const float* lw = wsm;
     const double coef = 2.0 * P.grad_loss[v] / ((double)(n - 2) * H * W);
     float* gs = P.grad_slices[v];
+    // pixels whose whole window lies in the interior class (2r from the
+    // border): sum_o w_o * orbit sum of (r_{m+1} + r_{m-1})
+    const bool row_in = V.cint >= 0 && y >= 2 * R && y <= H - 1 - 2 * R;
+    float orb[4][NO];
+    if (row_in) loo_orbits<R>(rup, rdn, lrow, lcol, orb);
+#pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int x = x0 + lcol + p;
         if (x >= W) break;
         float acc = 0.f;
+        if (row_in && x >= 2 * R && x <= W - 1 - 2 * R) {
+#pragma unroll
+            for (int o = 0; o < NO; ++o) acc = fmaf(wo[o], orb[p][o], acc);
+        } else {
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy) {
             const int qy = y - dy;
@@ -411,6 +528,7 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
                 acc = fmaf(wr[(0 * N2R + (dy + R)) * N2R + (dx + R)], rup[off], acc);  // S_m lower of m+1
                 acc = fmaf(wr[(1 * N2R + (dy + R)) * N2R + (dx + R)], rdn[off], acc);  // S_m upper of m-1
             }
+        }
         }
         double gval = (double)acc;
         if (m >= 1 && m <= n - 2) gval -= (double)res[(size_t)(m - 1) * plane + (size_t)y * W + x];
@@ -461,9 +579,10 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
         const int rows = LOO_TY + 2 * r;
         const int ntap = 2 * (2 * r + 1) * (2 * r + 1);
         const size_t ncls = (size_t)L.vol[v].ncx * L.vol[v].ncy;
-        size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4 + ncls * ntap * 4
+        (void)ncls;
+        size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4 + 25 * ntap * 4 + 16 * 4
                            : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + (32 * ntap + 2) * 4 + 8 * 8 +
-                                 ncls * ntap * 4 + 16;
+                                 25 * ntap * 4 + 16 * 4 + 16;
         if (b > m) m = b;
     }
     return m;
@@ -481,6 +600,8 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
         if (backward) {
             const size_t nb = (size_t)KRIG_LOO_REP * V.ncx * V.ncy * 2 * (2 * V.r + 1) * (2 * V.r + 1) * sizeof(double);
             e = cudaMemsetAsync(L.ws + V.lbar_off, 0, nb, st);
+            if (e != cudaSuccess) return (int)e;
+            e = cudaMemsetAsync(L.ws + V.lorb_off, 0, KRIG_LOO_REP * KRIG_NORB * sizeof(double), st);
             if (e != cudaSuccess) return (int)e;
         }
     }
