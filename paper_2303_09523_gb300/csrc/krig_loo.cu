@@ -247,6 +247,52 @@ __device__ __forceinline__ float loo_load(const void* in, int dtype, float scale
     return (float)((const double*)in)[idx];
 }
 
+// Four consecutive elements of a slice as float, starting at element idx
+// (idx and the row width multiples of 4, all four inside the row).
+__device__ __forceinline__ void loo_load4(const void* in, int dtype, float scale, size_t idx, float o[4])
+{
+    if (dtype == KRIG_F32) {
+        const float4 a = *(const float4*)((const float*)in + idx);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else if (dtype == KRIG_U16) {
+        const uint2 a = *(const uint2*)((const uint16_t*)in + idx);
+        o[0] = __fmul_rn((float)(a.x & 0xffffu), scale);
+        o[1] = __fmul_rn((float)(a.x >> 16), scale);
+        o[2] = __fmul_rn((float)(a.y & 0xffffu), scale);
+        o[3] = __fmul_rn((float)(a.y >> 16), scale);
+    } else {
+        const double2 a = *(const double2*)((const double*)in + idx), b = *(const double2*)((const double*)in + idx + 2);
+        o[0] = (float)a.x; o[1] = (float)a.y; o[2] = (float)b.x; o[3] = (float)b.y;
+    }
+}
+
+// A tile of ROWS rows x LOO_RP columns starting at (y0 - R, x0 - LOO_PAD) of
+// slice `plane_off` into shared memory, zeros outside the slice; four
+// columns per thread and step (LOO_PAD and the tile width are multiples of 4).
+template <int ROWS>
+__device__ __forceinline__ void loo_tile(const void* in, int dtype, float scale, size_t plane_off, int H, int W,
+                                         int ytop, int xleft, float* dst, int tid)
+{
+    constexpr int G = LOO_RP / 4;
+    const bool vec = (W & 3) == 0;
+    for (int e = tid; e < ROWS * G; e += 256) {
+        const int rr = e / G, cc = (e % G) * 4;
+        const int yy = ytop + rr, xx = xleft + cc;
+        float v4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (yy >= 0 && yy < H) {
+            const size_t row = plane_off + (size_t)yy * W;
+            if (vec && xx >= 0 && xx + 3 < W) {
+                loo_load4(in, dtype, scale, row + xx, v4);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (xx + q >= 0 && xx + q < W) v4[q] = loo_load(in, dtype, scale, row + xx + q);
+            }
+        }
+        *(float4*)(dst + rr * LOO_RP + cc) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+}
+
 // D4 orbit sums of a + b (two tiles with the residual-kernel layout) around
 // the four pixels of a thread: the LOO interior class is D4-symmetric and has
 // the same weights in both slices, so its stencil is sum_o w_o * orbit sum.
@@ -326,20 +372,27 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncls = V.ncx * V.ncy;
-    for (int e = tid; e < ROWS * LOO_RP; e += 256) {
-        const int rr = e / LOO_RP, cc = e % LOO_RP;
-        const int yy = y0 - R + rr, xx = x0 - LOO_PAD + cc;
-        float a = 0.f, b = 0.f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            a = loo_load(P.in[v], V.dtype, V.scale, (size_t)(j - 1) * plane + (size_t)yy * W + xx);
-            b = loo_load(P.in[v], V.dtype, V.scale, (size_t)(j + 1) * plane + (size_t)yy * W + xx);
+    loo_tile<ROWS>(P.in[v], V.dtype, V.scale, (size_t)(j - 1) * plane, H, W, y0 - R, x0 - LOO_PAD, lo, tid);
+    loo_tile<ROWS>(P.in[v], V.dtype, V.scale, (size_t)(j + 1) * plane, H, W, y0 - R, x0 - LOO_PAD, hi, tid);
+    {   // target slice: LOO_TY rows x LOO_TX columns from (y0, x0)
+        constexpr int G = LOO_TX / 4;
+        const bool vec = (W & 3) == 0;
+        for (int e = tid; e < LOO_TY * G; e += 256) {
+            const int rr = e / G, cc = (e % G) * 4;
+            const int yy = y0 + rr, xx = x0 + cc;
+            float v4[4] = {0.f, 0.f, 0.f, 0.f};
+            if (yy < H) {
+                const size_t row = (size_t)j * plane + (size_t)yy * W;
+                if (vec && xx + 3 < W) {
+                    loo_load4(P.in[v], V.dtype, V.scale, row + xx, v4);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (xx + q < W) v4[q] = loo_load(P.in[v], V.dtype, V.scale, row + xx + q);
+                }
+            }
+            *(float4*)(ce + rr * LOO_TX + cc) = make_float4(v4[0], v4[1], v4[2], v4[3]);
         }
-        lo[e] = a;
-        hi[e] = b;
-    }
-    for (int e = tid; e < LOO_TY * LOO_TX; e += 256) {
-        const int yy = y0 + e / LOO_TX, xx = x0 + e % LOO_TX;
-        ce[e] = (yy < H && xx < W) ? loo_load(P.in[v], V.dtype, V.scale, (size_t)j * plane + (size_t)yy * W + xx) : 0.f;
     }
     if (mode == 1)
         for (int e = tid; e < ncls * NTAP; e += 256) sg[e] = 0.f;
@@ -357,7 +410,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     float gio[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) gio[o] = 0.f;
-    double loss = 0.0;
+    float loss4 = 0.f;  // the thread's (at most four) squared residuals, FP32
     if (y < H) {
         // interior pixels: orbit sums of the two slices, one FMA per orbit
         const bool row_in = V.cint >= 0 && y >= R && y <= H - 1 - R;
@@ -387,7 +440,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
                         }
             }
             const float res = pred - ce[lrow * LOO_TX + lcol + p];
-            loss += (double)res * (double)res;
+            loss4 = fmaf(res, res, loss4);
             const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x;
             if (mode == 0) {
                 if (P.pred[v]) P.pred[v][oidx] = pred;
@@ -411,7 +464,8 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
             }
         }
     }
-    // loss: warp -> block -> volume accumulator
+    // loss: warp (FP64) -> block -> volume accumulator
+    double loss = (double)loss4;
     for (int o = 16; o; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
     if (lane == 0) sl[warp] = loss;
     if (mode == 1 && V.cint >= 0) {
@@ -476,17 +530,11 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool has_up = m + 1 <= n - 2, has_dn = m - 1 >= 1;
-    for (int e = tid; e < ROWS * LOO_RP; e += 256) {
-        const int rr = e / LOO_RP, cc = e % LOO_RP;
-        const int yy = y0 - R + rr, xx = x0 - LOO_PAD + cc;
-        float a = 0.f, b = 0.f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            if (has_up) a = res[(size_t)m * plane + (size_t)yy * W + xx];        // r_{m+1} at index m
-            if (has_dn) b = res[(size_t)(m - 2) * plane + (size_t)yy * W + xx];  // r_{m-1} at index m-2
-        }
-        rup[e] = a;
-        rdn[e] = b;
-    }
+    // r_{m+1} sits at residual index m, r_{m-1} at m-2 (zero tiles past the ends)
+    if (has_up) loo_tile<ROWS>(res, KRIG_F32, 1.0f, (size_t)m * plane, H, W, y0 - R, x0 - LOO_PAD, rup, tid);
+    else for (int e = tid; e < ROWS * LOO_RP; e += 256) rup[e] = 0.f;
+    if (has_dn) loo_tile<ROWS>(res, KRIG_F32, 1.0f, (size_t)(m - 2) * plane, H, W, y0 - R, x0 - LOO_PAD, rdn, tid);
+    else for (int e = tid; e < ROWS * LOO_RP; e += 256) rdn[e] = 0.f;
     {
         const float* lwg = (const float*)(P.ws + V.lw_off);
         for (int e = tid; e < V.ncx * V.ncy * NTAP; e += 256) wsm[e] = lwg[e];
@@ -499,6 +547,7 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     if (y >= H) return;
     const float* lw = wsm;
     const double coef = 2.0 * P.grad_loss[v] / ((double)(n - 2) * H * W);
+    const float fcoef = (float)coef;
     float* gs = P.grad_slices[v];
     // pixels whose whole window lies in the interior class (2r from the
     // border): sum_o w_o * orbit sum of (r_{m+1} + r_{m-1})
@@ -530,12 +579,12 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
             }
         }
         }
-        double gval = (double)acc;
-        if (m >= 1 && m <= n - 2) gval -= (double)res[(size_t)(m - 1) * plane + (size_t)y * W + x];
-        gval *= coef;
+        float gval = acc;  // FP32: the per-pixel terms need no FP64 (FP64 issues at 1/64 rate)
+        if (m >= 1 && m <= n - 2) gval -= res[(size_t)(m - 1) * plane + (size_t)y * W + x];
+        gval *= fcoef;
         const size_t oidx = (size_t)m * plane + (size_t)y * W + x;
-        if (P.accumulate) gs[oidx] += (float)gval;
-        else gs[oidx] = (float)gval;
+        if (P.accumulate) gs[oidx] += gval;
+        else gs[oidx] = gval;
     }
 }
 
