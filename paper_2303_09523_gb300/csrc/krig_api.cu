@@ -183,6 +183,13 @@ krig_status krig_plan_set_workspace(krig_plan_t plan, void* d_workspace, size_t 
                     (long long)plan->ws_bytes);
     cudaError_t e = cudaMemset(d_workspace, 0, 256);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the workspace control block");
+    if (plan->flags & KRIG_FLAG_LOO) {
+        // no LOO weights solved yet: the recorded variogram reads as NaN (matches nothing)
+        for (int v = 0; v < plan->L.n_vols; ++v) {
+            e = cudaMemset((unsigned char*)d_workspace + plan->L.vol[v].lvg_off, 0xff, sizeof(krig_variogram));
+            if (e != cudaSuccess) return cuda_fail(e, "initialising the LOO variogram record");
+        }
+    }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "clearing the workspace control block");
     plan->ws = (unsigned char*)d_workspace;

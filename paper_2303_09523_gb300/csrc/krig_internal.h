@@ -75,6 +75,7 @@ struct KrigVol {
     int64_t res_off;          // residuals (n-2) x H x W float
     int64_t lacc_off;         // loss accumulators, KRIG_LOO_REP doubles
     int64_t lorb_off;         // interior class: sum r * (orbit sum of both slices), [KRIG_LOO_REP][NORB] doubles
+    int64_t lvg_off;          // variogram the LOO weights were last solved for (krig_variogram)
 };
 
 struct KrigLaunch {
@@ -243,6 +244,8 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     *off = up(*off + KRIG_LOO_REP * 8);
     V.lorb_off = *off;
     *off = up(*off + KRIG_LOO_REP * KRIG_NORB * 8);
+    V.lvg_off = *off;
+    *off = up(*off + sizeof(krig_variogram));
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times

@@ -53,7 +53,10 @@ __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2
 }
 
 // ---------------------------------------------------------------------------
-// Class kernel: one block per (volume, xy-class).  mode 0: LOO weights.
+// Class kernel: one block per (volume, xy-class).  mode 0: LOO weights (and
+// a record of the variogram they were solved for).  mode 2: the same, unless
+// the record shows that the weights in the workspace already belong to this
+// variogram (the backward pass after the forward pass of the same step).
 // mode 1: weights and the adjoint contribution of this class to dL/dtheta.
 //
 // The two bracketing slices carry the same window and sit symmetrically
@@ -64,7 +67,7 @@ __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2
 // brackets, so only abar_lower + abar_upper = s_x - (1's_x / 1's_v) s_v enters,
 // with s_x from the same sum system at right-hand side wbar_lower + wbar_upper.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigLaunch P, int mode)
+__global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigLaunch P, int mode_in)
 {
     __shared__ ZSmem S;
     __shared__ double gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
@@ -81,6 +84,11 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     const int local = (int)(blockIdx.x - V.loo_cls_begin);
     const int cy = local / V.ncx, cx = local % V.ncx;
     const krig_variogram vg = P.vg[v];
+    krig_variogram* rec = (krig_variogram*)(P.ws + V.lvg_off);
+    if (mode_in == 2 && rec->model == vg.model && rec->nugget == vg.nugget && rec->sill == vg.sill &&
+        rec->range == vg.range)
+        return;  // these weights are already in the workspace
+    const int mode = mode_in == 1 ? 1 : 0;
     const int r = V.r, n2r = 2 * r + 1, nr = r + 1;
     const int g2 = 2 * V.g;  // LOO: bracketing slices 2g apart, target in the middle
     const int nC = 2 * n2r * n2r, n0 = 2 * nr * nr;
@@ -209,6 +217,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
             if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = (float)wgt[(dy + ly) * nx + (dx + lx)];
             lw[f] = w;
         }
+        if (tid == 0) *rec = vg;  // read by a later launch only
         return;
     }
     // dL/dtheta_p = sum_i abar_i (dc0_i/dtheta_p - sum_j d(A+B)_ij/dtheta_p w_j), i, j over the points
@@ -654,7 +663,7 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
             if (e != cudaSuccess) return (int)e;
         }
     }
-    k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, 0);
+    k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, backward ? 2 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     bool has_r[KRIG_RMAX + 1] = {};
     for (int v = 0; v < L.n_vols; ++v) has_r[L.vol[v].r] = true;
