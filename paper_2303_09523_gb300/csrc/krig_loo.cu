@@ -373,8 +373,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     float* lo = sm;
     float* hi = sm + ROWS * LOO_RP;
     float* ce = hi + ROWS * LOO_RP;                  // LOO_TY x LOO_TX, target slice
-    float* sg = ce + LOO_TY * LOO_TX;                // [ncls][NTAP] tap sums (mode 1)
-    double* sl = (double*)(sg + 32 * NTAP + 2);      // loss partials of the warps (8)
+    double* sl = (double*)(ce + LOO_TY * LOO_TX + 2);  // loss partials of the warps (8)
     float* wsm = (float*)(sl + 8);                   // [ncls][NTAP] LOO weights
     float* wo = wsm + 25 * NTAP;                     // interior weight per orbit
     float* sgo = wo + 8;                             // interior sum r * orbit sum (mode 1)
@@ -403,8 +402,6 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
             *(float4*)(ce + rr * LOO_TX + cc) = make_float4(v4[0], v4[1], v4[2], v4[3]);
         }
     }
-    if (mode == 1)
-        for (int e = tid; e < ncls * NTAP; e += 256) sg[e] = 0.f;
     {
         const float* lwg = (const float*)(P.ws + V.lw_off);
         for (int e = tid; e < ncls * NTAP; e += 256) wsm[e] = lwg[e];
@@ -455,20 +452,10 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
                 if (P.pred[v]) P.pred[v][oidx] = pred;
             } else {
                 ((float*)(P.ws + V.res_off))[oidx] = res;
+                // border classes: their tap sums are formed by k_loo_border from the stored residuals
                 if (inner) {
 #pragma unroll
                     for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < 2; ++s)
-#pragma unroll
-                        for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                            for (int dx = -R; dx <= R; ++dx) {
-                                const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
-                                const float z = (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx];
-                                atomicAdd(&sg[c * NTAP + k], res * z);
-                            }
                 }
             }
         }
@@ -492,12 +479,80 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
         for (int w = 0; w < 8; ++w) s += sl[w];
         atomicAdd((double*)(P.ws + V.lacc_off) + rep, s);
     }
-    if (mode == 1) {
-        double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * NTAP;
-        for (int e = tid; e < ncls * NTAP; e += 256)
-            if (sg[e] != 0.f) atomicAdd(lbar + e, (double)sg[e]);
-        if (V.cint >= 0 && tid < NO && sgo[tid] != 0.f)
-            atomicAdd((double*)(P.ws + V.lorb_off) + rep * KRIG_NORB + tid, (double)sgo[tid]);
+    if (mode == 1 && V.cint >= 0 && tid < NO && sgo[tid] != 0.f)
+        atomicAdd((double*)(P.ws + V.lorb_off) + rep * KRIG_NORB + tid, (double)sgo[tid]);
+}
+
+// ---------------------------------------------------------------------------
+// Tap sums sum_p r(p) S(p + d_k) of the border classes (backward pass): one
+// block per (volume, class, target slice j).  A class's pixels form a
+// rectangle (a row or column segment at the border, or one corner pixel);
+// each thread takes pixels of it and keeps one sum per tap, then the block
+// reduces them and adds them into one of the KRIG_LOO_REP copies.
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(128) k_loo_border(const __grid_constant__ KrigLaunch P)
+{
+    constexpr int N2R = 2 * R + 1, NTAP = 2 * N2R * N2R;
+    __shared__ float red[4][NTAP];
+    int64_t b = blockIdx.x, acc0 = 0;
+    int v = -1;
+    for (int u = 0; u < P.n_vols; ++u) {
+        const int64_t cnt = (int64_t)P.vol[u].ncx * P.vol[u].ncy * (P.vol[u].n - 2);
+        if (b < acc0 + cnt) {
+            v = u;
+            break;
+        }
+        acc0 += cnt;
+    }
+    if (v < 0) return;
+    const KrigVol& V = P.vol[v];
+    if (V.r != R) return;
+    const int ncls = V.ncx * V.ncy;
+    const int local = (int)(b - acc0), cls = local % ncls, j = 1 + local / ncls;
+    if (cls == V.cint) return;  // interior: orbit sums in the residual kernel
+    const int cy = cls / V.ncx, cx = cls % V.ncx;
+    const int H = V.H, W = V.W;
+    const int ly = V.yext[cy][0], ry = V.yext[cy][1], lx = V.xext[cx][0], rx = V.xext[cx][1];
+    // the class's rows and columns: a truncated side fixes the coordinate
+    const int ya = ly < R ? ly : (ry < R ? H - 1 - ry : R), yb = ly < R ? ly : (ry < R ? H - 1 - ry : H - 1 - R);
+    const int xa = lx < R ? lx : (rx < R ? W - 1 - rx : R), xb = lx < R ? lx : (rx < R ? W - 1 - rx : W - 1 - R);
+    const int nxr = xb - xa + 1, npx = (yb - ya + 1) * nxr;
+    const size_t plane = (size_t)H * W;
+    const float* res = (const float*)(P.ws + V.res_off) + (size_t)(j - 1) * plane;
+    float acc[NTAP];
+#pragma unroll
+    for (int k = 0; k < NTAP; ++k) acc[k] = 0.f;
+    for (int q = threadIdx.x; q < npx; q += 128) {
+        const int y = ya + q / nxr, x = xa + q % nxr;
+        const float rr = res[(size_t)y * W + x];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    if (dy < -ly || dy > ry || dx < -lx || dx > rx) continue;  // truncated tap
+                    const size_t idx = (size_t)(j - 1 + 2 * s) * plane + (size_t)(y + dy) * W + (x + dx);
+                    const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
+                    acc[k] = fmaf(rr, loo_load(P.in[v], V.dtype, V.scale, idx), acc[k]);
+                }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NTAP; ++k) {
+        float t = acc[k];
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NTAP) {
+        const float t = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+        if (t != 0.f) {
+            const int rep = (int)(blockIdx.x % KRIG_LOO_REP);
+            double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * NTAP;
+            atomicAdd(lbar + (int64_t)cls * NTAP + threadIdx.x, (double)t);
+        }
     }
 }
 
@@ -636,10 +691,8 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
         const int r = L.vol[v].r;
         const int rows = LOO_TY + 2 * r;
         const int ntap = 2 * (2 * r + 1) * (2 * r + 1);
-        const size_t ncls = (size_t)L.vol[v].ncx * L.vol[v].ncy;
-        (void)ncls;
         size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4 + 25 * ntap * 4 + 16 * 4
-                           : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + (32 * ntap + 2) * 4 + 8 * 8 +
+                           : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + 2 * 4 + 8 * 8 +
                                  25 * ntap * 4 + 16 * 4 + 16;
         if (b > m) m = b;
     }
@@ -678,6 +731,17 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
     if (!backward) {
         k_loo_finalize<<<1, 64, 0, st>>>(L);
         return (int)cudaGetLastError();
+    }
+    if (want_grad_params) {
+        int64_t nb = 0;
+        for (int v = 0; v < L.n_vols; ++v) nb += (int64_t)L.vol[v].ncx * L.vol[v].ncy * (L.vol[v].n - 2);
+        for (int r = 0; r <= KRIG_RMAX && nb > 0; ++r) {
+            if (!has_r[r]) continue;
+            if (r == 0) k_loo_border<0><<<(unsigned)nb, 128, 0, st>>>(L);
+            else if (r == 1) k_loo_border<1><<<(unsigned)nb, 128, 0, st>>>(L);
+            else k_loo_border<2><<<(unsigned)nb, 128, 0, st>>>(L);
+            if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        }
     }
     if (want_grad_slices) {
         const size_t s2 = loo_smem(L, 1);
