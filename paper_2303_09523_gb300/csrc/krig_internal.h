@@ -134,6 +134,9 @@ inline int64_t krig_wtab_bytes(const KrigVol& v)
 }
 inline int64_t krig_vtab_bytes(const KrigVol& v) { return (int64_t)v.ncx * v.ncy * KRIG_TSLOTS * 4; }
 #define KRIG_NORB 6  // D4 orbits of a (2r+1)^2 window for r <= 2
+// The LOO weight table [ncls][taps] is followed, at the next multiple of four
+// floats, by the interior class's weight per D4 orbit (8 slots).
+__host__ __device__ constexpr int loo_wo_off(int ntaps_all) { return (ntaps_all + 3) & ~3; }
 inline int64_t krig_otab_bytes(const KrigVol& v) { return 2LL * KRIG_NORB * KRIG_TSLOTS * (v.dtype == KRIG_F64 ? 8 : 4); }
 inline int64_t krig_lag_bytes(const KrigVol& v)
 {
@@ -235,7 +238,7 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     V.loo_adj_begin = *adj;
     *adj += (int64_t)V.n * tiles;
     V.lw_off = *off;
-    *off = up(*off + ncls * taps * 4);
+    *off = up(*off + (loo_wo_off((int)(ncls * taps)) + 8) * 4);
     V.lbar_off = *off;
     *off = up(*off + KRIG_LOO_REP * ncls * taps * 8);
     V.res_off = *off;

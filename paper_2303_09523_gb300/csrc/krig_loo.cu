@@ -24,6 +24,10 @@
 #define LOO_TY 16
 #define LOO_PAD 4
 #define LOO_RP (LOO_TX + 2 * LOO_PAD)
+// Shared-memory row stride of the tiles: 80 floats puts two consecutive rows
+// in opposite halves of the 32 banks, so the 16-byte loads of a quarter warp
+// (two rows x four 4-pixel groups) hit 32 distinct banks.
+#define LOO_SP 80
 
 // dC/d(nugget, sill, range) at squared lag h2 (C(h) = nugget + sill - gamma(h)).
 __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2, double d[3])
@@ -217,6 +221,21 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
             if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = (float)wgt[(dy + ly) * nx + (dx + lx)];
             lw[f] = w;
         }
+        if (local == V.cint && tid < (r + 1) * (r + 2) / 2) {
+            // interior class: weight per D4 orbit (mean over the orbit's taps of one
+            // slice), stored after the weight table for the stencil kernels
+            float sum = 0.f;
+            int cnt = 0;
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int qa = max(abs(dx), abs(dy)), qb = min(abs(dx), abs(dy));
+                    if (qa * (qa + 1) / 2 + qb == tid) {
+                        sum += (float)wgt[(dy + r) * n2r + (dx + r)];
+                        ++cnt;
+                    }
+                }
+            ((float*)(P.ws + V.lw_off))[loo_wo_off(V.ncx * V.ncy * 2 * nn) + tid] = sum / (float)cnt;
+        }
         if (tid == 0) *rec = vg;  // read by a later launch only
         return;
     }
@@ -275,30 +294,89 @@ __device__ __forceinline__ void loo_load4(const void* in, int dtype, float scale
     }
 }
 
-// A tile of ROWS rows x LOO_RP columns starting at (y0 - R, x0 - LOO_PAD) of
-// slice `plane_off` into shared memory, zeros outside the slice; four
-// columns per thread and step (LOO_PAD and the tile width are multiples of 4).
-template <int ROWS>
-__device__ __forceinline__ void loo_tile(const void* in, int dtype, float scale, size_t plane_off, int H, int W,
-                                         int ytop, int xleft, float* dst, int tid)
+// Tile staging in two phases: loo_fetch issues every global load of the
+// thread into registers, loo_commit converts and stores them to shared memory.
+// A block then waits for one memory latency per tile set instead of one per
+// loop step.  The tile is ROWS rows x 4G columns from (ytop, xleft) of slice
+// `plane_off`, zeros outside the slice (xleft, the row width and the slice
+// width multiples of 4 on the vector path).
+template <int ROWS, int G>
+struct LooStage {
+    static constexpr int NIT = (ROWS * G + 255) / 256;
+    uint4 raw[NIT];
+    unsigned conv;  // bit it: raw[it] holds four u16 values still to be scaled
+};
+
+template <int ROWS, int G>
+__device__ __forceinline__ void loo_fetch(const void* in, int dtype, float scale, size_t plane_off, int H, int W,
+                                          int ytop, int xleft, LooStage<ROWS, G>& st, int tid)
 {
-    constexpr int G = LOO_RP / 4;
-    const bool vec = (W & 3) == 0;
-    for (int e = tid; e < ROWS * G; e += 256) {
-        const int rr = e / G, cc = (e % G) * 4;
-        const int yy = ytop + rr, xx = xleft + cc;
-        float v4[4] = {0.f, 0.f, 0.f, 0.f};
-        if (yy >= 0 && yy < H) {
-            const size_t row = plane_off + (size_t)yy * W;
-            if (vec && xx >= 0 && xx + 3 < W) {
-                loo_load4(in, dtype, scale, row + xx, v4);
-            } else {
+    const bool vec = (W & 3) == 0 && dtype != KRIG_F64;
+    st.conv = 0u;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (xx + q >= 0 && xx + q < W) v4[q] = loo_load(in, dtype, scale, row + xx + q);
+    for (int it = 0; it < LooStage<ROWS, G>::NIT; ++it) {
+        const int e = tid + it * 256;
+        st.raw[it] = make_uint4(0u, 0u, 0u, 0u);
+        if (e >= ROWS * G) continue;
+        const int yy = ytop + e / G, xx = xleft + (e % G) * 4;
+        if (yy < 0 || yy >= H) continue;
+        const size_t row = plane_off + (size_t)yy * W;
+        if (vec && xx >= 0 && xx + 3 < W) {
+            if (dtype == KRIG_F32) {
+                st.raw[it] = *(const uint4*)((const float*)in + row + xx);
+            } else {
+                const uint2 a = *(const uint2*)((const uint16_t*)in + row + xx);
+                st.raw[it].x = a.x;
+                st.raw[it].y = a.y;
+                st.conv |= 1u << it;
             }
+        } else {
+            float f[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (xx + q >= 0 && xx + q < W) f[q] = loo_load(in, dtype, scale, row + xx + q);
+            st.raw[it] = make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]),
+                                    __float_as_uint(f[3]));
         }
-        *(float4*)(dst + rr * LOO_RP + cc) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+}
+
+template <int ROWS, int G>
+__device__ __forceinline__ void loo_commit(const LooStage<ROWS, G>& st, float scale, float* dst, int tid)
+{
+    static_assert(4 * G <= LOO_SP, "tile row wider than the shared-memory stride");
+#pragma unroll
+    for (int it = 0; it < LooStage<ROWS, G>::NIT; ++it) {
+        const int e = tid + it * 256;
+        if (e >= ROWS * G) continue;
+        const uint4 a = st.raw[it];
+        float4 f;
+        if ((st.conv >> it) & 1u) {
+            f.x = __fmul_rn((float)(a.x & 0xffffu), scale);
+            f.y = __fmul_rn((float)(a.x >> 16), scale);
+            f.z = __fmul_rn((float)(a.y & 0xffffu), scale);
+            f.w = __fmul_rn((float)(a.y >> 16), scale);
+        } else {
+            f = make_float4(__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z), __uint_as_float(a.w));
+        }
+        *(float4*)(dst + (e / G) * LOO_SP + (e % G) * 4) = f;
+    }
+}
+
+// The LOO weight table and the orbit weights after it (nw floats, a multiple
+// of four, at most 2048) into shared memory, loads first.
+__device__ __forceinline__ void loo_copy_weights(const float* lwg, int nw, float* dst, int tid)
+{
+    float4 a[2];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int e = tid + it * 256;
+        a[it] = e * 4 < nw ? ((const float4*)lwg)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int e = tid + it * 256;
+        if (e * 4 < nw) ((float4*)dst)[e] = a[it];
     }
 }
 
@@ -311,15 +389,24 @@ template <int R>
 __device__ __forceinline__ void loo_orbits(const float* a, const float* b, int lrow, int lcol,
                                            float (&o)[4][LooNO<R>::N])
 {
+    static_assert(LOO_PAD == 4 && R <= 4, "window columns lcol - 4 .. lcol + 7 cover the taps");
     constexpr int NC = 4 + 2 * R;
     float F[2 * R + 1][NC];
 #pragma unroll
-    for (int dy = -R; dy <= R; ++dy)
+    for (int dy = -R; dy <= R; ++dy) {
+        // the 16-byte-aligned columns lcol - 4 .. lcol + 7 of both rows, three vector loads each
+        const int base = (lrow + R + dy) * LOO_SP + lcol;
+        float wa[12], wb[12];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            const int idx = (lrow + R + dy) * LOO_RP + LOO_PAD + lcol + k - R;
-            F[dy + R][k] = a[idx] + b[idx];
+        for (int q = 0; q < 3; ++q) {
+            if (R == 0 && q != 1) continue;
+            const float4 u = *(const float4*)(a + base + 4 * q), t = *(const float4*)(b + base + 4 * q);
+            wa[4 * q] = u.x; wa[4 * q + 1] = u.y; wa[4 * q + 2] = u.z; wa[4 * q + 3] = u.w;
+            wb[4 * q] = t.x; wb[4 * q + 1] = t.y; wb[4 * q + 2] = t.z; wb[4 * q + 3] = t.w;
         }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) F[dy + R][k] = wa[4 - R + k] + wb[4 - R + k];
+    }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int m = R + p;
@@ -337,31 +424,6 @@ __device__ __forceinline__ void loo_orbits(const float* a, const float* b, int l
     }
 }
 
-// Orbit index of an in-plane offset and the interior class's weight per orbit
-// (the mean over the orbit's taps of one slice; both slices are equal).
-__device__ __forceinline__ int loo_orbit(int dx, int dy)
-{
-    const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy));
-    return a * (a + 1) / 2 + b;
-}
-
-template <int R>
-__device__ __forceinline__ void loo_orbit_weights(const float* wrow, float* wo, int tid)
-{
-    constexpr int N2R = 2 * R + 1;
-    if (tid < LooNO<R>::N) {
-        float sum = 0.f;
-        int cnt = 0;
-        for (int dy = -R; dy <= R; ++dy)
-            for (int dx = -R; dx <= R; ++dx)
-                if (loo_orbit(dx, dy) == tid) {
-                    sum += wrow[(dy + R) * N2R + (dx + R)];
-                    ++cnt;
-                }
-        wo[tid] = sum / (float)cnt;
-    }
-}
-
 template <int R>
 __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int y0, int mode, float* sm)
 {
@@ -371,41 +433,25 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     const int H = V.H, W = V.W;
     const size_t plane = (size_t)H * W;
     float* lo = sm;
-    float* hi = sm + ROWS * LOO_RP;
-    float* ce = hi + ROWS * LOO_RP;                  // LOO_TY x LOO_TX, target slice
-    double* sl = (double*)(ce + LOO_TY * LOO_TX + 2);  // loss partials of the warps (8)
-    float* wsm = (float*)(sl + 8);                   // [ncls][NTAP] LOO weights
-    float* wo = wsm + 25 * NTAP;                     // interior weight per orbit
-    float* sgo = wo + 8;                             // interior sum r * orbit sum (mode 1)
+    float* hi = sm + ROWS * LOO_SP;
+    float* ce = hi + ROWS * LOO_SP;                   // LOO_TY x LOO_TX, target slice
+    float* wsm = ce + LOO_TY * LOO_SP;                // [ncls][NTAP] LOO weights, orbit weights
+    float* sgo = wsm + loo_wo_off(25 * NTAP) + 8;     // interior sum r * orbit sum (mode 1)
+    double* sl = (double*)(sgo + 8);                  // loss partials of the warps (8)
     constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncls = V.ncx * V.ncy;
-    loo_tile<ROWS>(P.in[v], V.dtype, V.scale, (size_t)(j - 1) * plane, H, W, y0 - R, x0 - LOO_PAD, lo, tid);
-    loo_tile<ROWS>(P.in[v], V.dtype, V.scale, (size_t)(j + 1) * plane, H, W, y0 - R, x0 - LOO_PAD, hi, tid);
-    {   // target slice: LOO_TY rows x LOO_TX columns from (y0, x0)
-        constexpr int G = LOO_TX / 4;
-        const bool vec = (W & 3) == 0;
-        for (int e = tid; e < LOO_TY * G; e += 256) {
-            const int rr = e / G, cc = (e % G) * 4;
-            const int yy = y0 + rr, xx = x0 + cc;
-            float v4[4] = {0.f, 0.f, 0.f, 0.f};
-            if (yy < H) {
-                const size_t row = (size_t)j * plane + (size_t)yy * W;
-                if (vec && xx + 3 < W) {
-                    loo_load4(P.in[v], V.dtype, V.scale, row + xx, v4);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (xx + q < W) v4[q] = loo_load(P.in[v], V.dtype, V.scale, row + xx + q);
-                }
-            }
-            *(float4*)(ce + rr * LOO_TX + cc) = make_float4(v4[0], v4[1], v4[2], v4[3]);
-        }
-    }
+    const float* wo = wsm + loo_wo_off(ncls * NTAP);  // interior weight per orbit
     {
-        const float* lwg = (const float*)(P.ws + V.lw_off);
-        for (int e = tid; e < ncls * NTAP; e += 256) wsm[e] = lwg[e];
-        if (V.cint >= 0) loo_orbit_weights<R>(lwg + (int64_t)V.cint * NTAP, wo, tid);
+        LooStage<ROWS, LOO_RP / 4> a, b;
+        LooStage<LOO_TY, LOO_TX / 4> c;
+        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)(j - 1) * plane, H, W, y0 - R, x0 - LOO_PAD, a, tid);
+        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)(j + 1) * plane, H, W, y0 - R, x0 - LOO_PAD, b, tid);
+        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)j * plane, H, W, y0, x0, c, tid);
+        loo_copy_weights((const float*)(P.ws + V.lw_off), loo_wo_off(ncls * NTAP) + 8, wsm, tid);
+        loo_commit(a, V.scale, lo, tid);
+        loo_commit(b, V.scale, hi, tid);
+        loo_commit(c, V.scale, ce, tid);
         if (tid < 8) sgo[tid] = 0.f;
     }
     __syncthreads();
@@ -417,46 +463,76 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
 #pragma unroll
     for (int o = 0; o < NO; ++o) gio[o] = 0.f;
     float loss4 = 0.f;  // the thread's (at most four) squared residuals, FP32
+    float outv[4] = {0.f, 0.f, 0.f, 0.f};
     if (y < H) {
+        float cev[4];
+        {
+            const float4 c4 = *(const float4*)(ce + lrow * LOO_SP + lcol);
+            cev[0] = c4.x; cev[1] = c4.y; cev[2] = c4.z; cev[3] = c4.w;
+        }
         // interior pixels: orbit sums of the two slices, one FMA per orbit
         const bool row_in = V.cint >= 0 && y >= R && y <= H - 1 - R;
         float orb[4][NO];
         if (row_in) loo_orbits<R>(lo, hi, lrow, lcol, orb);
-        const int cy = V.ymap[krig_slot(y, H, R)];
+        // residual, loss term and output of pixel p; interior pixels also feed the
+        // orbit sums of dL/dw (border classes: k_loo_border, from the stored residuals)
+        const auto finish = [&](int p, float pred, bool inner) {
+            const float res = pred - cev[p];
+            loss4 = fmaf(res, res, loss4);
+            outv[p] = mode == 0 ? pred : res;
+            if (mode == 1 && inner) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int x = x0 + lcol + p;
-            if (x >= W) break;
-            const int c = cy * V.ncx + V.xmap[krig_slot(x, W, R)];
-            const bool inner = row_in && c == V.cint;
-            float pred = 0.f;
-            if (inner) {
+                for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
+            }
+        };
+        if (row_in && x0 + lcol >= R && x0 + lcol + 3 <= W - 1 - R) {
+            // all four pixels in the interior class
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                float pred = 0.f;
 #pragma unroll
                 for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
-            } else {
-                const float* wr = lw + (int64_t)c * NTAP;
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                        for (int dx = -R; dx <= R; ++dx) {
-                            const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
-                            pred = fmaf(wr[k], (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_RP + LOO_PAD + lcol + p + dx], pred);
-                        }
+                finish(p, pred, true);
             }
-            const float res = pred - ce[lrow * LOO_TX + lcol + p];
-            loss4 = fmaf(res, res, loss4);
-            const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x;
-            if (mode == 0) {
-                if (P.pred[v]) P.pred[v][oidx] = pred;
-            } else {
-                ((float*)(P.ws + V.res_off))[oidx] = res;
-                // border classes: their tap sums are formed by k_loo_border from the stored residuals
+        } else {
+            const int cy = V.ymap[krig_slot(y, H, R)];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int x = x0 + lcol + p;
+                if (x >= W) break;
+                const int c = cy * V.ncx + V.xmap[krig_slot(x, W, R)];
+                const bool inner = row_in && c == V.cint;
+                float pred = 0.f;
                 if (inner) {
 #pragma unroll
-                    for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
+                    for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
+                } else {
+                    const float* wr = lw + (int64_t)c * NTAP;
+#pragma unroll
+                    for (int s = 0; s < 2; ++s)
+#pragma unroll
+                        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                            for (int dx = -R; dx <= R; ++dx) {
+                                const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
+                                pred = fmaf(wr[k], (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_SP + LOO_PAD + lcol + p + dx],
+                                            pred);
+                            }
                 }
+                finish(p, pred, inner);
+            }
+        }
+        // predictions (mode 0, when asked for) or residuals (mode 1): one vector store
+        // when the four pixels are in the slice and the row is 16-byte aligned
+        float* dst = mode == 0 ? P.pred[v] : (float*)(P.ws + V.res_off);
+        if (dst) {
+            const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x0 + lcol;
+            if ((W & 3) == 0 && x0 + lcol + 3 < W) {
+                *(float4*)(dst + oidx) = make_float4(outv[0], outv[1], outv[2], outv[3]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    if (x0 + lcol + p < W) dst[oidx + p] = outv[p];
             }
         }
     }
@@ -559,7 +635,7 @@ __global__ void __launch_bounds__(128) k_loo_border(const __grid_constant__ Krig
 // One instance per half-width r (the tap arrays set the register budget);
 // blocks of volumes with another r leave at once.
 template <int R>
-__global__ void __launch_bounds__(256, R == 2 ? 2 : 4) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
+__global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
 {
     extern __shared__ __align__(16) float lsm[];
     const int64_t it = blockIdx.x;
@@ -588,42 +664,59 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     const size_t plane = (size_t)H * W;
     const float* res = (const float*)(P.ws + V.res_off);  // r_j at (j-1)
     float* rup = sm;                   // r_{m+1}: predictions for which S_m is the lower slice
-    float* rdn = sm + ROWS * LOO_RP;   // r_{m-1}: predictions for which S_m is the upper slice
-    float* wsm = rdn + ROWS * LOO_RP;  // [ncls][NTAP] LOO weights
-    float* wo = wsm + 25 * NTAP;       // interior weight per orbit
+    float* rdn = sm + ROWS * LOO_SP;   // r_{m-1}: predictions for which S_m is the upper slice
+    float* wsm = rdn + ROWS * LOO_SP;  // [ncls][NTAP] LOO weights, orbit weights
     constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float* wo = wsm + loo_wo_off(V.ncx * V.ncy * NTAP);  // interior weight per orbit
     const bool has_up = m + 1 <= n - 2, has_dn = m - 1 >= 1;
-    // r_{m+1} sits at residual index m, r_{m-1} at m-2 (zero tiles past the ends)
-    if (has_up) loo_tile<ROWS>(res, KRIG_F32, 1.0f, (size_t)m * plane, H, W, y0 - R, x0 - LOO_PAD, rup, tid);
-    else for (int e = tid; e < ROWS * LOO_RP; e += 256) rup[e] = 0.f;
-    if (has_dn) loo_tile<ROWS>(res, KRIG_F32, 1.0f, (size_t)(m - 2) * plane, H, W, y0 - R, x0 - LOO_PAD, rdn, tid);
-    else for (int e = tid; e < ROWS * LOO_RP; e += 256) rdn[e] = 0.f;
-    {
-        const float* lwg = (const float*)(P.ws + V.lw_off);
-        for (int e = tid; e < V.ncx * V.ncy * NTAP; e += 256) wsm[e] = lwg[e];
-        if (V.cint >= 0) loo_orbit_weights<R>(lwg + (int64_t)V.cint * NTAP, wo, tid);
-    }
-    __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int y = y0 + lrow;
+    float* gs = P.grad_slices[v];
+    float rc[4], gprev[4];
+    {
+        // r_{m+1} sits at residual index m, r_{m-1} at m-2 (zero tiles past the ends:
+        // the fetch of a row outside 0..H-1 loads nothing)
+        LooStage<ROWS, LOO_RP / 4> a, b;
+        loo_fetch(res, KRIG_F32, 1.0f, (size_t)(has_up ? m : 0) * plane, has_up ? H : 0, W, y0 - R, x0 - LOO_PAD, a,
+                  tid);
+        loo_fetch(res, KRIG_F32, 1.0f, (size_t)(has_dn ? m - 2 : 0) * plane, has_dn ? H : 0, W, y0 - R,
+                  x0 - LOO_PAD, b, tid);
+        loo_copy_weights((const float*)(P.ws + V.lw_off), loo_wo_off(V.ncx * V.ncy * NTAP) + 8, wsm, tid);
+        // the thread's own residuals r_m and (accumulating) the previous gradient, loaded
+        // with the tiles
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int x = x0 + lcol + p;
+            rc[p] = 0.f;
+            gprev[p] = 0.f;
+            if (y < H && x < W) {
+                if (m >= 1 && m <= n - 2) rc[p] = res[(size_t)(m - 1) * plane + (size_t)y * W + x];
+                if (P.accumulate) gprev[p] = gs[(size_t)m * plane + (size_t)y * W + x];
+            }
+        }
+        loo_commit(a, 1.0f, rup, tid);
+        loo_commit(b, 1.0f, rdn, tid);
+    }
+    __syncthreads();
     if (y >= H) return;
     const float* lw = wsm;
     const double coef = 2.0 * P.grad_loss[v] / ((double)(n - 2) * H * W);
     const float fcoef = (float)coef;
-    float* gs = P.grad_slices[v];
     // pixels whose whole window lies in the interior class (2r from the
     // border): sum_o w_o * orbit sum of (r_{m+1} + r_{m-1})
     const bool row_in = V.cint >= 0 && y >= 2 * R && y <= H - 1 - 2 * R;
     float orb[4][NO];
     if (row_in) loo_orbits<R>(rup, rdn, lrow, lcol, orb);
+    float outv[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool all_in = row_in && x0 + lcol >= 2 * R && x0 + lcol + 3 <= W - 1 - 2 * R;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int x = x0 + lcol + p;
-        if (x >= W) break;
+        if (!all_in && x >= W) break;
         float acc = 0.f;
-        if (row_in && x >= 2 * R && x <= W - 1 - 2 * R) {
+        if (all_in || (row_in && x >= 2 * R && x <= W - 1 - 2 * R)) {
 #pragma unroll
             for (int o = 0; o < NO; ++o) acc = fmaf(wo[o], orb[p][o], acc);
         } else {
@@ -637,23 +730,28 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
                 const int qx = x - dx;
                 if (qx < 0 || qx >= W) continue;
                 const float* wr = lw + (int64_t)(cyq * V.ncx + V.xmap[krig_slot(qx, W, R)]) * NTAP;
-                const int off = (lrow + R - dy) * LOO_RP + LOO_PAD + lcol + p - dx;
+                const int off = (lrow + R - dy) * LOO_SP + LOO_PAD + lcol + p - dx;
                 acc = fmaf(wr[(0 * N2R + (dy + R)) * N2R + (dx + R)], rup[off], acc);  // S_m lower of m+1
                 acc = fmaf(wr[(1 * N2R + (dy + R)) * N2R + (dx + R)], rdn[off], acc);  // S_m upper of m-1
             }
         }
         }
-        float gval = acc;  // FP32: the per-pixel terms need no FP64 (FP64 issues at 1/64 rate)
-        if (m >= 1 && m <= n - 2) gval -= res[(size_t)(m - 1) * plane + (size_t)y * W + x];
-        gval *= fcoef;
-        const size_t oidx = (size_t)m * plane + (size_t)y * W + x;
-        if (P.accumulate) gs[oidx] += gval;
-        else gs[oidx] = gval;
+        // FP32: the per-pixel terms need no FP64 (FP64 issues at 1/64 rate)
+        const float gval = (acc - rc[p]) * fcoef;
+        outv[p] = P.accumulate ? gprev[p] + gval : gval;
+    }
+    const size_t oidx = (size_t)m * plane + (size_t)y * W + x0 + lcol;
+    if ((W & 3) == 0 && x0 + lcol + 3 < W) {
+        *(float4*)(gs + oidx) = make_float4(outv[0], outv[1], outv[2], outv[3]);
+    } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            if (x0 + lcol + p < W) gs[oidx + p] = outv[p];
     }
 }
 
 template <int R>
-__global__ void __launch_bounds__(256, R == 2 ? 2 : 4) k_loo_adjoint(const __grid_constant__ KrigLaunch P)
+__global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_adjoint(const __grid_constant__ KrigLaunch P)
 {
     extern __shared__ __align__(16) float lsm[];
     const int64_t it = blockIdx.x;
@@ -691,9 +789,9 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
         const int r = L.vol[v].r;
         const int rows = LOO_TY + 2 * r;
         const int ntap = 2 * (2 * r + 1) * (2 * r + 1);
-        size_t b = adjoint ? (size_t)2 * rows * LOO_RP * 4 + 25 * ntap * 4 + 16 * 4
-                           : (size_t)2 * rows * LOO_RP * 4 + LOO_TY * LOO_TX * 4 + 2 * 4 + 8 * 8 +
-                                 25 * ntap * 4 + 16 * 4 + 16;
+        const size_t wcap = (size_t)loo_wo_off(25 * ntap) + 8;  // weights + orbit weights
+        size_t b = adjoint ? ((size_t)2 * rows * LOO_SP + wcap) * 4
+                           : ((size_t)2 * rows * LOO_SP + LOO_TY * LOO_SP + wcap + 8) * 4 + 8 * 8;
         if (b > m) m = b;
     }
     return m;
