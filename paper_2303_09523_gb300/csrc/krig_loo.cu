@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     __shared__ double dC[3][2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
     __shared__ double d0[3][2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
     __shared__ double wgt[ZN], abar[ZN], red[8][4];
+    __shared__ double tsum[ZN], osum[KRIG_NORB];  // mode 1: tap and orbit sums over the copies
+    static_assert(KRIG_LOO_REP == 32, "one copy per lane in the reductions below");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int v = 0;
@@ -135,16 +137,32 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
         S.dy[e] = (int8_t)(e < n ? e / nx - ly : 0);
     }
+    if (mode == 1) {
+        // sum r S_k of each point over both slices and the KRIG_LOO_REP copies: one
+        // warp per point, one copy per lane; the interior orbit sums likewise
+        for (int i = warp; i < n; i += 8) {
+            const int dx = i % nx - lx, dy = i / nx - ly;
+            double t = 0.0;
+            for (int s = 0; s < 2; ++s) t += lbar[lane * lrep + (s * n2r + (dy + r)) * n2r + (dx + r)];
+            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) tsum[i] = t;
+        }
+        if (local == V.cint && warp == 7) {
+            const double* lorb = (const double*)(P.ws + V.lorb_off);
+            for (int o = 0; o < (r + 1) * (r + 2) / 2; ++o) {
+                double t = lorb[lane * KRIG_NORB + o];
+                for (int k = 16; k; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+                if (lane == 0) osum[o] = t;
+            }
+        }
+        __syncthreads();
+    }
     for (int i = tid; i < n; i += 256) {
         const int dx = i % nx - lx, dy = i / nx - ly;
         S.B[0][i][0] = 2.0 * g0[abs(dy) * nr + abs(dx)];
         S.B[0][i][1] = 2.0;
         if (mode == 1) {
-            double sum = 0.0;
-            for (int s = 0; s < 2; ++s) {
-                const int full = (s * n2r + (dy + r)) * n2r + (dx + r);
-                for (int c = 0; c < KRIG_LOO_REP; ++c) sum += lbar[c * lrep + full];
-            }
+            double sum = tsum[i];
             if (local == V.cint) {
                 // interior class: the residual kernel kept only orbit sums (both
                 // slices); dL/dtheta depends on wbar only through them (the class
@@ -157,10 +175,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
                         const int qa = max(abs(qx), abs(qy)), qb = min(abs(qx), abs(qy));
                         cnt += (qa * (qa + 1) / 2 + qb) == o;
                     }
-                const double* lorb = (const double*)(P.ws + V.lorb_off);
-                double g = 0.0;
-                for (int c = 0; c < KRIG_LOO_REP; ++c) g += lorb[c * KRIG_NORB + o];
-                sum += g / cnt;
+                sum += osum[o] / cnt;
             }
             S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
         }
@@ -240,16 +255,22 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         return;
     }
     // dL/dtheta_p = sum_i abar_i (dc0_i/dtheta_p - sum_j d(A+B)_ij/dtheta_p w_j), i, j over the points
+    // eight threads per point i, each over every eighth j
     double tp3[3] = {0.0, 0.0, 0.0};
-    for (int i = tid; i < n; i += 256) {
-        const int dxi = S.dx[i], dyi = S.dy[i];
-        const int i0 = abs(dyi) * nr + abs(dxi);
-        double acc[3] = {d0[0][i0], d0[1][i0], d0[2][i0]};
-        for (int j = 0; j < n; ++j) {
-            const int ic = abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j]);
-            for (int p = 0; p < 3; ++p) acc[p] -= (dC[p][ic] + dC[p][nn + ic]) * wgt[j];
+    {
+        const int i = tid >> 3, q = tid & 7;
+        if (i < n) {
+            const int dxi = S.dx[i], dyi = S.dy[i];
+            const int i0 = abs(dyi) * nr + abs(dxi);
+            double acc[3] = {0.0, 0.0, 0.0};
+            if (q == 0)
+                for (int p = 0; p < 3; ++p) acc[p] = d0[p][i0];
+            for (int j = q; j < n; j += 8) {
+                const int ic = abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j]);
+                for (int p = 0; p < 3; ++p) acc[p] -= (dC[p][ic] + dC[p][nn + ic]) * wgt[j];
+            }
+            for (int p = 0; p < 3; ++p) tp3[p] = abar[i] * acc[p];
         }
-        for (int p = 0; p < 3; ++p) tp3[p] += abar[i] * acc[p];
     }
     for (int p = 0; p < 3; ++p)
         for (int o = 16; o; o >>= 1) tp3[p] += __shfl_xor_sync(0xffffffffu, tp3[p], o);
