@@ -24,6 +24,9 @@
 // Device status bits (sticky, in the workspace control block).
 #define KRIG_DEV_SINGULAR 0x1u
 #define KRIG_DEV_TIMEOUT 0x2u
+// Byte offset in the (zeroed) workspace control block of the LOO forward
+// launch's block ticket counter (reset by the launch's last block).
+#define KRIG_CTRL_LOO_DONE 64
 
 // n / d for 0 <= n < 2^32 by one multiply-high with m = krig_udiv_magic(d):
 // m = ceil(2^64 / d), and floor(n m / 2^64) = floor(n / d) because the error

@@ -90,6 +90,18 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     const int local = (int)(blockIdx.x - V.loo_cls_begin);
     const int cy = local / V.ncx, cx = local % V.ncx;
     const krig_variogram vg = P.vg[v];
+    if (mode_in != 1) {
+        // a new pass: zero the volume's loss sums and (backward) the dL/dw sums, spread
+        // over its class blocks; the kernels that add to them run after this launch
+        const int ncls = V.ncx * V.ncy, taps = 2 * (2 * V.r + 1) * (2 * V.r + 1);
+        for (int e = local * 256 + tid; e < KRIG_LOO_REP; e += ncls * 256) ((double*)(P.ws + V.lacc_off))[e] = 0.0;
+        if (mode_in == 2) {
+            for (int e = local * 256 + tid; e < KRIG_LOO_REP * ncls * taps; e += ncls * 256)
+                ((double*)(P.ws + V.lbar_off))[e] = 0.0;
+            for (int e = local * 256 + tid; e < KRIG_LOO_REP * KRIG_NORB; e += ncls * 256)
+                ((double*)(P.ws + V.lorb_off))[e] = 0.0;
+        }
+    }
     krig_variogram* rec = (krig_variogram*)(P.ws + V.lvg_off);
     if (mode_in == 2 && rec->model == vg.model && rec->nugget == vg.nugget && rec->sill == vg.sill &&
         rec->range == vg.range)
@@ -286,8 +298,9 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
 
 // ---------------------------------------------------------------------------
 // Residual kernel: one block per (volume, target slice j, 64 x 16 tile).
-// mode 0: loss (and optional prediction).  mode 1: loss, residual buffer and
-// the per-class tap sums sum r S_k for dL/dw.
+// mode 0: loss (and optional prediction).  mode 1: residual buffer and the
+// interior class's sums r * (orbit sum) for dL/dw (the border classes' tap sums
+// are formed from the stored residuals by loo_border_block).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float loo_load(const void* in, int dtype, float scale, size_t idx)
 {
@@ -496,7 +509,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
         float orb[4][NO];
         if (row_in) loo_orbits<R>(lo, hi, lrow, lcol, orb);
         // residual, loss term and output of pixel p; interior pixels also feed the
-        // orbit sums of dL/dw (border classes: k_loo_border, from the stored residuals)
+        // orbit sums of dL/dw (border classes: loo_border_block, from the stored residuals)
         const auto finish = [&](int p, float pred, bool inner) {
             const float res = pred - cev[p];
             loss4 = fmaf(res, res, loss4);
@@ -582,20 +595,22 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
 
 // ---------------------------------------------------------------------------
 // Tap sums sum_p r(p) S(p + d_k) of the border classes (backward pass): one
-// block per (volume, class, target slice j).  A class's pixels form a
-// rectangle (a row or column segment at the border, or one corner pixel);
-// each thread takes pixels of it and keeps one sum per tap, then the block
-// reduces them and adds them into one of the KRIG_LOO_REP copies.
+// block per (volume, class, target slice j, bracketing slice s).  A class's
+// pixels form a rectangle (a row or column segment at the border, or one
+// corner pixel); each thread takes pixels of it and keeps one sum per tap of
+// slice s, then the block reduces them and adds them into one of the
+// KRIG_LOO_REP copies.  Runs as the first blocks of the gradient launch.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t loo_border_blocks(const KrigVol& V) { return 2LL * V.ncx * V.ncy * (V.n - 2); }
+
 template <int R>
-__global__ void __launch_bounds__(128) k_loo_border(const __grid_constant__ KrigLaunch P)
+__device__ void loo_border_block(const KrigLaunch& P, int64_t b, float* sm)
 {
-    constexpr int N2R = 2 * R + 1, NTAP = 2 * N2R * N2R;
-    __shared__ float red[4][NTAP];
-    int64_t b = blockIdx.x, acc0 = 0;
+    constexpr int N2R = 2 * R + 1, NT = N2R * N2R;  // taps of one slice
+    int64_t acc0 = 0;
     int v = -1;
     for (int u = 0; u < P.n_vols; ++u) {
-        const int64_t cnt = (int64_t)P.vol[u].ncx * P.vol[u].ncy * (P.vol[u].n - 2);
+        const int64_t cnt = loo_border_blocks(P.vol[u]);
         if (b < acc0 + cnt) {
             v = u;
             break;
@@ -606,7 +621,7 @@ __global__ void __launch_bounds__(128) k_loo_border(const __grid_constant__ Krig
     const KrigVol& V = P.vol[v];
     if (V.r != R) return;
     const int ncls = V.ncx * V.ncy;
-    const int local = (int)(b - acc0), cls = local % ncls, j = 1 + local / ncls;
+    const int local = (int)(b - acc0), cls = local % ncls, s = (local / ncls) & 1, j = 1 + local / (2 * ncls);
     if (cls == V.cint) return;  // interior: orbit sums in the residual kernel
     const int cy = cls / V.ncx, cx = cls % V.ncx;
     const int H = V.H, W = V.W;
@@ -617,38 +632,38 @@ __global__ void __launch_bounds__(128) k_loo_border(const __grid_constant__ Krig
     const int nxr = xb - xa + 1, npx = (yb - ya + 1) * nxr;
     const size_t plane = (size_t)H * W;
     const float* res = (const float*)(P.ws + V.res_off) + (size_t)(j - 1) * plane;
-    float acc[NTAP];
+    const size_t sl = (size_t)(j - 1 + 2 * s) * plane;  // slice j - 1 (s = 0) or j + 1 (s = 1)
+    float acc[NT];
 #pragma unroll
-    for (int k = 0; k < NTAP; ++k) acc[k] = 0.f;
-    for (int q = threadIdx.x; q < npx; q += 128) {
+    for (int k = 0; k < NT; ++k) acc[k] = 0.f;
+    for (int q = threadIdx.x; q < npx; q += 256) {
         const int y = ya + q / nxr, x = xa + q % nxr;
         const float rr = res[(size_t)y * W + x];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
-            for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                for (int dx = -R; dx <= R; ++dx) {
-                    if (dy < -ly || dy > ry || dx < -lx || dx > rx) continue;  // truncated tap
-                    const size_t idx = (size_t)(j - 1 + 2 * s) * plane + (size_t)(y + dy) * W + (x + dx);
-                    const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
-                    acc[k] = fmaf(rr, loo_load(P.in[v], V.dtype, V.scale, idx), acc[k]);
-                }
+            for (int dx = -R; dx <= R; ++dx) {
+                if (dy < -ly || dy > ry || dx < -lx || dx > rx) continue;  // truncated tap
+                const int k = (dy + R) * N2R + (dx + R);
+                acc[k] = fmaf(rr, loo_load(P.in[v], V.dtype, V.scale, sl + (size_t)(y + dy) * W + (x + dx)), acc[k]);
+            }
     }
+    float* red = sm;  // [8][NT]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < NTAP; ++k) {
+    for (int k = 0; k < NT; ++k) {
         float t = acc[k];
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[warp][k] = t;
+        if (lane == 0) red[warp * NT + k] = t;
     }
     __syncthreads();
-    if (threadIdx.x < NTAP) {
-        const float t = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    if (threadIdx.x < NT) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += red[w * NT + threadIdx.x];
         if (t != 0.f) {
-            const int rep = (int)(blockIdx.x % KRIG_LOO_REP);
-            double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * NTAP;
-            atomicAdd(lbar + (int64_t)cls * NTAP + threadIdx.x, (double)t);
+            const int rep = (int)(b % KRIG_LOO_REP);
+            double* lbar = (double*)(P.ws + V.lbar_off) + (int64_t)rep * ncls * 2 * NT;
+            atomicAdd(lbar + (int64_t)cls * 2 * NT + s * NT + threadIdx.x, (double)t);
         }
     }
 }
@@ -670,6 +685,29 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_residual(const __gr
     const int tile = (int)(local % tiles);
     const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
     if (V.r == R) loo_residual_tile<R>(P, v, j, x0, y0, mode, lsm);
+    if (mode != 0) return;
+    // forward: the last block of the launch turns the loss sums of the volumes
+    // with this r into their losses (thread 0 of every block made its loss
+    // atomic before its fence and ticket); the ticket counter resets itself
+    __shared__ unsigned last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned* done = (unsigned*)(P.ws + KRIG_CTRL_LOO_DONE);
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int u = threadIdx.x; u < P.n_vols; u += blockDim.x) {
+        const KrigVol& U = P.vol[u];
+        if (U.r != R) continue;
+        const double* acc = (const double*)(P.ws + U.lacc_off);
+        double sum = 0.0;
+        for (int c = 0; c < KRIG_LOO_REP; ++c) sum += __ldcg(acc + c);
+        P.loss[u] = sum / ((double)(U.n - 2) * U.H * U.W);
+    }
+    if (threadIdx.x == 0) *(unsigned*)(P.ws + KRIG_CTRL_LOO_DONE) = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -771,11 +809,18 @@ __device__ void loo_adjoint_tile(const KrigLaunch& P, int v, int m, int x0, int 
     }
 }
 
+// Gradient launch: blocks [0, nborder) form the border-class tap sums (dL/dw,
+// for dL/dtheta), the rest the adjoint w.r.t. the slices; both read only the
+// residuals, so they share one launch.
 template <int R>
-__global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_adjoint(const __grid_constant__ KrigLaunch P)
+__global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_grad(const __grid_constant__ KrigLaunch P, int64_t nborder)
 {
     extern __shared__ __align__(16) float lsm[];
-    const int64_t it = blockIdx.x;
+    if ((int64_t)blockIdx.x < nborder) {
+        loo_border_block<R>(P, blockIdx.x, lsm);
+        return;
+    }
+    const int64_t it = blockIdx.x - nborder;
     int v = 0;
     for (int u = 1; u < P.n_vols; ++u)
         if (P.vol[u].loo_adj_begin <= it) v = u;
@@ -787,17 +832,6 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_adjoint(const __gri
     const int tile = (int)(local % tiles);
     const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
     if (V.r == R) loo_adjoint_tile<R>(P, v, m, x0, y0, lsm);
-}
-
-__global__ void k_loo_finalize(const __grid_constant__ KrigLaunch P)
-{
-    const int v = threadIdx.x;
-    if (v >= P.n_vols) return;
-    const KrigVol& V = P.vol[v];
-    const double* acc = (const double*)(P.ws + V.lacc_off);
-    double s = 0.0;
-    for (int c = 0; c < KRIG_LOO_REP; ++c) s += acc[c];
-    P.loss[v] = s / ((double)(V.n - 2) * V.H * V.W);
 }
 
 // ---------------------------------------------------------------------------
@@ -822,19 +856,7 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
 {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
-    // zero the loss accumulators and (backward) the tap sums
-    for (int v = 0; v < L.n_vols; ++v) {
-        const KrigVol& V = L.vol[v];
-        e = cudaMemsetAsync(L.ws + V.lacc_off, 0, KRIG_LOO_REP * sizeof(double), st);
-        if (e != cudaSuccess) return (int)e;
-        if (backward) {
-            const size_t nb = (size_t)KRIG_LOO_REP * V.ncx * V.ncy * 2 * (2 * V.r + 1) * (2 * V.r + 1) * sizeof(double);
-            e = cudaMemsetAsync(L.ws + V.lbar_off, 0, nb, st);
-            if (e != cudaSuccess) return (int)e;
-            e = cudaMemsetAsync(L.ws + V.lorb_off, 0, KRIG_LOO_REP * KRIG_NORB * sizeof(double), st);
-            if (e != cudaSuccess) return (int)e;
-        }
-    }
+    // the class launch also zeroes the accumulators of the pass
     k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, backward ? 2 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     bool has_r[KRIG_RMAX + 1] = {};
@@ -847,28 +869,18 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
         else k_loo_residual<2><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     }
-    if (!backward) {
-        k_loo_finalize<<<1, 64, 0, st>>>(L);
-        return (int)cudaGetLastError();
-    }
-    if (want_grad_params) {
-        int64_t nb = 0;
-        for (int v = 0; v < L.n_vols; ++v) nb += (int64_t)L.vol[v].ncx * L.vol[v].ncy * (L.vol[v].n - 2);
-        for (int r = 0; r <= KRIG_RMAX && nb > 0; ++r) {
-            if (!has_r[r]) continue;
-            if (r == 0) k_loo_border<0><<<(unsigned)nb, 128, 0, st>>>(L);
-            else if (r == 1) k_loo_border<1><<<(unsigned)nb, 128, 0, st>>>(L);
-            else k_loo_border<2><<<(unsigned)nb, 128, 0, st>>>(L);
-            if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
-        }
-    }
-    if (want_grad_slices) {
+    if (!backward) return 0;
+    int64_t nb = 0;
+    if (want_grad_params)
+        for (int v = 0; v < L.n_vols; ++v) nb += loo_border_blocks(L.vol[v]);
+    const int64_t na = want_grad_slices ? L.n_loo_adj : 0;
+    if (nb + na > 0) {
         const size_t s2 = loo_smem(L, 1);
         for (int r = 0; r <= KRIG_RMAX; ++r) {
             if (!has_r[r]) continue;
-            if (r == 0) k_loo_adjoint<0><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
-            else if (r == 1) k_loo_adjoint<1><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
-            else k_loo_adjoint<2><<<(unsigned)L.n_loo_adj, 256, s2, st>>>(L);
+            if (r == 0) k_loo_grad<0><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
+            else if (r == 1) k_loo_grad<1><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
+            else k_loo_grad<2><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
             if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
         }
     }
