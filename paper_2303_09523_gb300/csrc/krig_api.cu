@@ -289,10 +289,7 @@ krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const k
     L.loss = nullptr;
     L.accumulate = accumulate ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
-    if (d_grad_params && !accumulate) {
-        cudaError_t e = cudaMemsetAsync(d_grad_params, 0, sizeof(double) * 3 * L.n_vols, st);
-        if (e != cudaSuccess) return cuda_fail(e, "clearing d_grad_params");
-    }
+    // d_grad_params is cleared (unless accumulating) by the first launch of the pass
     return timed_launch(plan, st, 3, [&] { return krig_launch_loo(L, 1, want_slices, d_grad_params != nullptr, st); },
                         "backward launch");
 }

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
                 ((double*)(P.ws + V.lbar_off))[e] = 0.0;
             for (int e = local * 256 + tid; e < KRIG_LOO_REP * KRIG_NORB; e += ncls * 256)
                 ((double*)(P.ws + V.lorb_off))[e] = 0.0;
+            if (P.grad_params && !P.accumulate && local == 0 && tid < 3) P.grad_params[3 * v + tid] = 0.0;
         }
     }
     krig_variogram* rec = (krig_variogram*)(P.ws + V.lvg_off);
