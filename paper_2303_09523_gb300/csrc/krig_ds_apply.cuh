@@ -762,8 +762,28 @@ __device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsVol
 // instructions with no stores and no slot release, run while the class solve
 // is still going, so that the code is in the instruction caches when the
 // real pass starts (it is cold after the L2 has been flushed).
+// The class solve may still be running (programmatic dependent launch): wait
+// for it to complete, then copy the interior orbit weights of all volumes,
+// now final, into shared memory; a named barrier over the consumer warps only
+// (the producer runs on).  Every consumer warp calls this exactly once: before
+// its first real item, or after its last shape if it had none.
+template <typename TI>
+__device__ __noinline__ void ds_weights_ready(const KrigLaunch& P, int dtype)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    TC* owsm = (TC*)DsLayout<TI>::shared().ow;
+    const int nv = P.n_vols;
+    constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
+    for (int e = threadIdx.x; e < nv * NW; e += DS_CONSUMERS * 32) {
+        const KrigVol& Vv = P.vol[e / NW];
+        owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(P.ws + Vv.otab_off))[e % NW] : TC(0);
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
+}
+
 template <typename TI, int R, int GM1>
-__device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, int lane, bool dry)
+__device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, int lane, bool dry, bool* pending)
 {
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     const DsShared sh = DsLayout<TI>::shared();
@@ -783,6 +803,11 @@ __device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, i
         DsItem d;
         if (!VR.match || !ds_decode_r(VR, it, d)) continue;
         if (*(volatile int*)sh.abort) break;
+        if (!dry && *pending) {
+            // the item's constants and decode are done: only now wait for the weights
+            ds_weights_ready<TI>(P, dtype);
+            *pending = false;
+        }
         ds_consume_item<TI, R, GM1>(P, VR, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane, dry);
         if (dry) break;
         q += d.c1 - d.c0 + 1;
@@ -791,17 +816,17 @@ __device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, i
 }
 
 template <typename TI, int R>
-__device__ __forceinline__ int ds_run_g(int g, const KrigLaunch& P, int q, int warp, int lane, bool dry)
+__device__ __forceinline__ int ds_run_g(int g, const KrigLaunch& P, int q, int warp, int lane, bool dry, bool* pending)
 {
     switch (g) {
-    case 1: return ds_run_shape<TI, R, 0>(P, q, warp, lane, dry);
-    case 2: return ds_run_shape<TI, R, 1>(P, q, warp, lane, dry);
-    case 3: return ds_run_shape<TI, R, 2>(P, q, warp, lane, dry);
-    case 4: return ds_run_shape<TI, R, 3>(P, q, warp, lane, dry);
-    case 5: return ds_run_shape<TI, R, 4>(P, q, warp, lane, dry);
-    case 6: return ds_run_shape<TI, R, 5>(P, q, warp, lane, dry);
-    case 7: return ds_run_shape<TI, R, 6>(P, q, warp, lane, dry);
-    default: return ds_run_shape<TI, R, 7>(P, q, warp, lane, dry);
+    case 1: return ds_run_shape<TI, R, 0>(P, q, warp, lane, dry, pending);
+    case 2: return ds_run_shape<TI, R, 1>(P, q, warp, lane, dry, pending);
+    case 3: return ds_run_shape<TI, R, 2>(P, q, warp, lane, dry, pending);
+    case 4: return ds_run_shape<TI, R, 3>(P, q, warp, lane, dry, pending);
+    case 5: return ds_run_shape<TI, R, 4>(P, q, warp, lane, dry, pending);
+    case 6: return ds_run_shape<TI, R, 5>(P, q, warp, lane, dry, pending);
+    case 7: return ds_run_shape<TI, R, 6>(P, q, warp, lane, dry, pending);
+    default: return ds_run_shape<TI, R, 7>(P, q, warp, lane, dry, pending);
     }
 }
 
@@ -849,9 +874,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     constexpr int stride = DsLayout<TI>::stride;
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
     TI* slots = DsLayout<TI>::slots();
-    typedef typename DsTypes<TI>::TC TC;
     const DsShared sh = DsLayout<TI>::shared();
-    TC* owsm = (TC*)sh.ow;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < DS_STAGES) {
         mbar_init(&sh.full[tid], 1);
@@ -906,20 +929,22 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     }
     if (warp < DS_CONSUMERS) {
         // warm-up pass while the class solve may still run (first shape only)
+        bool none = false;
         for (int c = 0; c < DS_NSHAPE; ++c) {
             if (!((shapes >> c) & 1u)) continue;
             const int r = c / 8, g = c % 8 + 1;
-            if (r == 0) ds_run_g<TI, 0>(g, P, 0, warp, lane, true);
-            else if (r == 1) ds_run_g<TI, 1>(g, P, 0, warp, lane, true);
-            else ds_run_g<TI, 2>(g, P, 0, warp, lane, true);
+            if (r == 0) ds_run_g<TI, 0>(g, P, 0, warp, lane, true, &none);
+            else if (r == 1) ds_run_g<TI, 1>(g, P, 0, warp, lane, true, &none);
+            else ds_run_g<TI, 2>(g, P, 0, warp, lane, true, &none);
             break;
         }
     }
-    // The class solve may still be running (programmatic dependent launch):
-    // wait for it to complete before the first read of the weight tables.
-    // The producer warp streams input slices only and does not wait.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (warp == DS_FRAMER) {
+        // The class solve may still be running (programmatic dependent launch):
+        // wait for it to complete before the first read of the weight tables.
+        // The producer warp streams input slices only and does not wait; the
+        // consumer warps wait in ds_weights_ready.
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         // ---------------- frame warp: border pixels (within r of the slice
         // edge, their own truncation classes), latency-bound reads through L2,
         // beside the consumers' tiles
@@ -938,17 +963,6 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
         return;
     }
     // ---------------- consumer warps
-    // the interior orbit weights, now final, into shared memory; a named
-    // barrier over the consumer warps only (the producer runs on)
-    {
-        const int nv = P.n_vols;
-        constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
-        for (int e = tid; e < nv * NW; e += DS_CONSUMERS * 32) {
-            const KrigVol& Vv = P.vol[e / NW];
-            owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(P.ws + Vv.otab_off))[e % NW] : TC(0);
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
-    }
     if (P.fault_timeout && blockIdx.x == 0 && warp == 0) {
         // test hook: wait on a barrier nothing completes; the bounded wait gives up
         if (!mbar_wait(sh.never, 0, 1u << 12) && lane == 0) {
@@ -957,13 +971,15 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
         }
     }
     int q = 0;
+    bool pending = true;  // weights not yet waited for (ds_weights_ready)
     for (int c = 0; c < DS_NSHAPE; ++c) {
         if (!((shapes >> c) & 1u)) continue;
         const int r = c / 8, g = c % 8 + 1;
-        if (r == 0) q = ds_run_g<TI, 0>(g, P, q, warp, lane, false);
-        else if (r == 1) q = ds_run_g<TI, 1>(g, P, q, warp, lane, false);
-        else q = ds_run_g<TI, 2>(g, P, q, warp, lane, false);
+        if (r == 0) q = ds_run_g<TI, 0>(g, P, q, warp, lane, false, &pending);
+        else if (r == 1) q = ds_run_g<TI, 1>(g, P, q, warp, lane, false, &pending);
+        else q = ds_run_g<TI, 2>(g, P, q, warp, lane, false, &pending);
     }
+    if (pending) ds_weights_ready<TI>(P, dtype);  // no item: still one arrival at the barrier
     (void)slots;
 }
 

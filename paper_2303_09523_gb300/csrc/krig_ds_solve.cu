@@ -333,22 +333,18 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
         if (V.dtype == KRIG_F64) ((double*)(P.ws + V.wtab_off))[row + e] = w;
         else ((float*)(P.ws + V.wtab_off))[row + e] = (float)w;
     }
-    // interior class: weights per D4 orbit (mean over the orbit's members)
+    // interior class: weight per D4 orbit.  The class is D4-symmetric, so the
+    // members of an orbit carry the same weight up to rounding; the table takes
+    // the member (dx, dy) = (a, b) of orbit (a, b), a >= b >= 0.
     if (cy * V.ncx + cx == V.cint) {
         for (int e = tid; e < 2 * KRIG_NORB * KRIG_TSLOTS; e += NT) {
             const int c = e % KRIG_TSLOTS, o = (e / KRIG_TSLOTS) % KRIG_NORB, s = e / (KRIG_TSLOTS * KRIG_NORB);
-            double sum = 0.0;
-            int cnt = 0;
-            if (c < g - 1) {
-                for (int dy = -r; dy <= r; ++dy)
-                    for (int dx = -r; dx <= r; ++dx) {
-                        const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy));
-                        if (a * (a + 1) / 2 + b != o) continue;
-                        sum += ok ? S.W[s][(dy + ly) * nx + dx + lx][c] : qnan;
-                        ++cnt;
-                    }
+            double w = 0.0;
+            if (c < g - 1 && o < (r + 1) * (r + 2) / 2) {
+                int oa, ob;
+                ds_pair(o, &oa, &ob);
+                w = ok ? S.W[s][(ob + ly) * nx + oa + lx][c] * scale : qnan;
             }
-            const double w = cnt ? sum / cnt * scale : 0.0;
             if (V.dtype == KRIG_F64) ((double*)(P.ws + V.otab_off))[e] = w;
             else ((float*)(P.ws + V.otab_off))[e] = (float)w;
         }
