@@ -168,7 +168,11 @@ krig_status krig_loo_forward(krig_plan_t plan, const void* const* d_slices, cons
  *   - the variogram parameters (d_grad_params: nullable device float64
  *     [n_vols][3] = d/d(nugget, sill, range)).
  * With accumulate != 0 the gradients are added to the buffers; otherwise they
- * are overwritten.  The class systems are solved again rather than stored.
+ * are overwritten.  The residuals are recomputed from the slices, not kept
+ * from the forward pass; the LOO class weights are reused when the workspace
+ * records that they were solved for the same variogram values (the forward
+ * pass of the same step), and solved again otherwise; the class adjoint
+ * systems are always solved again.
  * Errors: as krig_loo_forward. */
 krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const krig_variogram* d_params,
                           const double* d_grad_loss, float* const* d_grad_slices, double* d_grad_params,
