@@ -204,3 +204,20 @@ def test_loo_batched_volumes_mixed_r():
         assert _nw(preds[i].double().cpu().numpy(), ref["pred"]) <= 1e-5, i
         assert _nw(gp[3 * i:3 * i + 3].cpu().numpy(), ref["grad_theta"]) <= 1e-4, i
         assert _nw(gs[i].double().cpu().numpy(), ref["grad_slices"]) <= 1e-4, i
+
+
+@pytest.mark.parametrize("n,H,W,g,r,model", [
+    (3, 3, 5, 2, 2, "spherical"),        # one target slice; window wider than the slice: no interior class
+    (4, 2, 9, 3, 1, "exponential"),      # two rows: every pixel is a border pixel
+    (3, 17, 6, 4, 0, "spherical"),       # r = 0 (two-point midpoint); width not a multiple of 4
+    (5, 70, 131, 2, 2, "exponential"),   # several tiles with ragged right and bottom tails
+])
+def test_loo_edge_geometries(n, H, W, g, r, model):
+    vol = phantoms.random_stack(n, H, W, g, r, k=1, seed=70 + n + H, model=model)
+    theta = dict(model=model, nugget=0.03, sill=vol.sill, range=4.0)
+    got, vals = _run(vol, theta)
+    ref = oracle.loo(vals, g, r, want_pred=True, want_grad_theta=True, want_grad_slices=True, **theta)
+    assert got["loss"] == pytest.approx(ref["loss"], rel=1e-5)
+    assert _nw(got["pred"], ref["pred"]) <= 1e-5
+    assert _nw(got["grad_theta"], ref["grad_theta"]) <= 1e-4
+    assert _nw(got["grad_slices"], ref["grad_slices"]) <= 1e-4
