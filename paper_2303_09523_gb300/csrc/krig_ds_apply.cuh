@@ -803,12 +803,17 @@ __device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, i
         DsItem d;
         if (!VR.match || !ds_decode_r(VR, it, d)) continue;
         if (*(volatile int*)sh.abort) break;
-        if (!dry && *pending) {
-            // the item's constants and decode are done: only now wait for the weights
-            ds_weights_ready<TI>(P, dtype);
-            *pending = false;
+        // First item of the warp: a warm-up pass over its first gap (same code, no
+        // stores) while the class solve may still run, so the consumer code is
+        // cached when the weights arrive; only then the wait (ds_weights_ready).
+        for (int pass = (!dry && *pending) ? 0 : 1; pass < 2; ++pass) {
+            if (pass == 1 && !dry && *pending) {
+                ds_weights_ready<TI>(P, dtype);
+                *pending = false;
+            }
+            ds_consume_item<TI, R, GM1>(P, VR, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane,
+                                        dry || pass == 0);
         }
-        ds_consume_item<TI, R, GM1>(P, VR, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane, dry);
         if (dry) break;
         q += d.c1 - d.c0 + 1;
     }
@@ -926,18 +931,6 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
                 mbar_wait(&sh.full[qq % DS_STAGES], (qq / DS_STAGES) & 1, DS_WAIT_LIMIT);
         }
         return;
-    }
-    if (warp < DS_CONSUMERS) {
-        // warm-up pass while the class solve may still run (first shape only)
-        bool none = false;
-        for (int c = 0; c < DS_NSHAPE; ++c) {
-            if (!((shapes >> c) & 1u)) continue;
-            const int r = c / 8, g = c % 8 + 1;
-            if (r == 0) ds_run_g<TI, 0>(g, P, 0, warp, lane, true, &none);
-            else if (r == 1) ds_run_g<TI, 1>(g, P, 0, warp, lane, true, &none);
-            else ds_run_g<TI, 2>(g, P, 0, warp, lane, true, &none);
-            break;
-        }
     }
     if (warp == DS_FRAMER) {
         // The class solve may still be running (programmatic dependent launch):
