@@ -7,8 +7,10 @@ the CUDA library (``paper_2303_09523_gb300``) and neither imports the other.
 
 The arithmetic lives in ``krig_oracle.c`` (Gaussian elimination with partial
 pivoting on the bordered ordinary-kriging system, Appendix A with one constant
-predictor; sub-block layout of Algorithm 1).  This module only marshals numpy
-arrays through ctypes.
+predictor; sub-block layout of Algorithm 1).  This module marshals numpy arrays
+through ctypes, and holds one numpy function of its own:
+``empirical_variogram`` (the method-of-moments semivariogram of the known
+slices, the data the variogram of Sec. 4.1.2 is fitted to).
 """
 import ctypes
 import os
@@ -186,3 +188,39 @@ def loo(slices, g, r, threads=0, want_pred=False, want_grad_theta=False, want_gr
     if want_grad_slices:
         out["grad_slices"] = gs
     return out
+
+
+def empirical_variogram(slices, max_lag):
+    """Sums of squared increments of the known slices per lag vector, and pair counts.
+
+    The paper uses a variogram gamma(h) (Sec. 4.1.2) without saying how it is
+    estimated; the classical method-of-moments estimate is
+    gamma(h) = sum over pairs (z_i - z_j)^2 / (2 N(h)).  Lag vectors here are
+    (dx, dy) in pixels, |dx|, |dy| <= max_lag, within one known slice (s = 0)
+    or from known slice k to k + 1 (s = 1).  For each (s, dy, dx):
+        sums[s, dy+L, dx+L]   = sum_{k, y, x} (S[k, y, x] - S[k+s, y+dy, x+dx])^2
+        counts[s, dy+L, dx+L] = number of terms (both voxels inside the stack),
+    summed in float64 over whole arrays (numpy).
+    """
+    S = np.asarray(slices, dtype=np.float64)
+    n, H, W = S.shape
+    L = int(max_lag)
+    q = 2 * L + 1
+    sums = np.zeros((2, q, q))
+    counts = np.zeros((2, q, q), dtype=np.int64)
+    for s in (0, 1):
+        if n - s <= 0:
+            continue
+        for dy in range(-L, L + 1):
+            ya, yb = max(0, -dy), min(H, H - dy)  # y with 0 <= y + dy < H
+            for dx in range(-L, L + 1):
+                xa, xb = max(0, -dx), min(W, W - dx)
+                if yb <= ya or xb <= xa:
+                    continue
+                a = S[0:n - s, ya:yb, xa:xb]
+                b = S[s:n, ya + dy:yb + dy, xa + dx:xb + dx]
+                d = a - b
+                sums[s, dy + L, dx + L] = float(np.sum(d * d))
+                counts[s, dy + L, dx + L] = d.size
+    return sums, counts
+

@@ -342,3 +342,56 @@ def test_loo_grad_homogeneity():
     vg0 = dict(vg, nugget=0.0)
     gt0 = oracle.loo(s, 3, 1, want_grad_theta=True, **vg0)["grad_theta"]
     assert abs(gt0[1]) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# empirical variogram (method-of-moments semivariogram of the known slices)
+# ---------------------------------------------------------------------------
+def test_empirical_variogram_brute_force():
+    S = np.random.default_rng(11).normal(size=(3, 5, 7))
+    L = 2
+    sums, counts = oracle.empirical_variogram(S, L)
+    n, H, W = S.shape
+    for s in (0, 1):
+        for dy in range(-L, L + 1):
+            for dx in range(-L, L + 1):
+                tot, cnt = 0.0, 0
+                for k in range(n - s):
+                    for y in range(H):
+                        for x in range(W):
+                            if 0 <= y + dy < H and 0 <= x + dx < W:
+                                tot += (S[k, y, x] - S[k + s, y + dy, x + dx]) ** 2
+                                cnt += 1
+                assert counts[s, dy + L, dx + L] == cnt
+                assert sums[s, dy + L, dx + L] == pytest.approx(tot, rel=1e-12, abs=1e-300)
+
+
+def test_empirical_variogram_linear_ramp_closed_form():
+    """S = a x + b y + c k: every pair at lag (dx, dy, s) differs by a dx + b dy + c s, so
+    gamma = (a dx + b dy + c s)^2 / 2 and the counts are (n - s)(H - |dy|)(W - |dx|)."""
+    n, H, W, L = 4, 9, 11, 3
+    a, b, c = 0.7, -0.3, 1.9
+    k, y, x = np.meshgrid(np.arange(n), np.arange(H), np.arange(W), indexing="ij")
+    S = a * x + b * y + c * k
+    sums, counts = oracle.empirical_variogram(S, L)
+    for s in (0, 1):
+        for dy in range(-L, L + 1):
+            for dx in range(-L, L + 1):
+                N = (n - s) * (H - abs(dy)) * (W - abs(dx))
+                assert counts[s, dy + L, dx + L] == N
+                gam = sums[s, dy + L, dx + L] / (2 * N)
+                assert gam == pytest.approx((a * dx + b * dy + c * s) ** 2 / 2, rel=1e-12, abs=1e-12)
+
+
+def test_empirical_variogram_constant_and_symmetry():
+    n, H, W, L = 3, 6, 5, 2
+    sums, counts = oracle.empirical_variogram(np.full((n, H, W), 3.25), L)
+    assert np.all(sums == 0.0) and np.all(counts > 0)
+    S = np.random.default_rng(12).normal(size=(n, H, W))
+    sums, _ = oracle.empirical_variogram(S, L)
+    # within one slice the pair sets of (dx, dy) and (-dx, -dy) are the same pairs
+    assert np.allclose(sums[0], sums[0][::-1, ::-1], rtol=1e-12, atol=0)
+    assert sums[0, L, L] == 0.0  # zero lag
+    # lags past the slice give no pairs
+    sums, counts = oracle.empirical_variogram(np.zeros((2, 2, 3)), 3)
+    assert counts[0, 3, 0] == 0 and counts[0, 3 + 2, 3] == 0 and counts[1, 3, 3] == 2 * 3
