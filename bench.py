@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--no-fit", action="store_true", help="use the default variogram instead of the LOO fit")
     ap.add_argument("--no-loo", action="store_true", help="skip the leave-one-slice-out fwd+bwd timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-volume batched graph-replay timing")
+    ap.add_argument("--no-variogram", action="store_true", help="skip the empirical-variogram timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -332,6 +333,9 @@ def main():
         extra["fwd_bwd"] = time_loo(args, vol, s_dev, desc, params, dev, stream, flush)
     if rank == 0 and not args.no_batch:
         extra["batched"] = time_batch(args, dev, stream, flush)
+    if rank == 0 and not args.no_variogram:
+        extra["empirical_variogram"] = time_variogram(args, vol, s_dev, stream, flush,
+                                                      extra.get("alu_peaks_measured"))
     if variogram_fit is not None:
         extra["variogram_fit"] = variogram_fit
 
@@ -409,6 +413,37 @@ def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
             "replay": "CUDA graph of loo_forward + backward",
             "voxels_per_step": nvox, "loss": float(loss.item()),
             "grad_theta": [float(x) for x in gp.cpu()]}
+
+
+def time_variogram(args, vol, s_dev, stream, flush, peaks, max_lag=8):
+    """Method-of-moments variogram data of the workload's known slices (krig_empirical_variogram):
+    squared-increment sums for every lag vector |dx|, |dy| <= 8 within a slice and to the next slice.
+    FP32-pipe bound: a subtract and a fused multiply-add per voxel pair."""
+    import torch
+    from paper_2303_09523_gb300 import binding
+    for _ in range(max(3, args.warmup)):
+        sums, counts = binding.empirical_variogram(s_dev, max_lag, in_scale=vol.in_scale, stream=stream)
+    evs = []
+    steps = min(args.steps, 50)
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        binding.empirical_variogram(s_dev, max_lag, in_scale=vol.in_scale, stream=stream)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    pairs = int(counts.sum())
+    out = {"value": pairs / (ms * 1e-3), "unit": "voxel pairs/s", "ms_per_call": ms, "max_lag": max_lag,
+           "lag_vectors": int(counts.size), "pairs_per_call": pairs}
+    if peaks:
+        peak = peaks["fp32_fma_gflops"] * 1e9 / 2 / 2  # FP32 instructions/s, two per pair
+        out["roofline"] = {"bound": "alu", "achieved": pairs / (ms * 1e-3), "peak": peak, "unit": "pairs/s",
+                           "frac": pairs / (ms * 1e-3) / peak,
+                           "peak_source": "measured FP32 FMA rate / 2 instructions per pair"}
+    return out
 
 
 def time_batch(args, dev, stream, flush):

@@ -239,6 +239,29 @@ void krig_plan_destroy(krig_plan_t plan);
 krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out, float* d_var,
                                      const krig_variogram* d_params, int32_t check_status, void* stream);
 
+/* Empirical variogram of the known slices: the method-of-moments estimate of
+ * the variogram gamma(h) that Sec. 4.1.2 uses (the paper does not say how it is
+ * obtained), i.e. the data a model (spherical, exponential) is fitted to.
+ * For every lag vector (s, dy, dx), |dy|, |dx| <= L = max_lag, s = 0 (both
+ * voxels in one known slice) or s = 1 (known slice k to known slice k + 1):
+ *   d_sums[(s (2L+1) + dy+L) (2L+1) + dx+L]
+ *       = sum over k, y, x with both voxels inside the stack of
+ *         (S[k][y][x] - S[k+s][y+dy][x+dx])^2
+ * (device float64, 2 (2L+1)^2 entries, overwritten) and, if h_counts is not
+ * NULL, the number of such pairs in the same layout (host int64, filled before
+ * the call returns); gamma = sums / (2 counts) where counts > 0.  The in-plane
+ * lags are in pixels; slice k + 1 lies zfactor output voxels above slice k.
+ *   desc: H, W, n_known, in_dtype, in_scale as for krig_plan_create
+ *         (zfactor, n_sub_blocks and half_w are not used).
+ *   d_slices: n_known x H x W of in_dtype (u16: value * in_scale).
+ *   max_lag: 0..16.
+ * Differences and squares in float32, summed over at most 64 pixels of a row
+ * in float32 and above that in float64.  Asynchronous on `stream`; no
+ * workspace, no allocation.  Errors: KRIG_EINVAL (before any launch),
+ * KRIG_ECUDA. */
+krig_status krig_empirical_variogram(const krig_volume_desc* desc, const void* d_slices, int32_t max_lag,
+                                     double* d_sums, int64_t* h_counts, void* stream);
+
 /* Measure the device's fused multiply-add rate (GFLOP/s, 2 flops per FMA)
  * in FP32 (fp64 = 0) or FP64 (fp64 = 1) on the current device with a short
  * synchronous kernel.  Support routine: the roofline denominator for kernels

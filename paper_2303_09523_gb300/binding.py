@@ -90,6 +90,9 @@ def lib(build_if_missing: bool = False):
     L.krig_measure_fma_peak.restype = ctypes.c_int
     L.krig_version.argtypes = []
     L.krig_version.restype = ctypes.c_int32
+    L.krig_empirical_variogram.argtypes = [ctypes.POINTER(VolumeDesc), vp, ctypes.c_int32, vp,
+                                           ctypes.POINTER(ctypes.c_int64), vp]
+    L.krig_empirical_variogram.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -242,6 +245,27 @@ def measure_fma_peak(fp64: bool) -> float:
     g = ctypes.c_double()
     _check(lib().krig_measure_fma_peak(1 if fp64 else 0, ctypes.byref(g)))
     return g.value
+
+
+def empirical_variogram(slices, max_lag, in_scale=1.0, stream=None):
+    """Method-of-moments variogram data of a known-slice stack (device tensor n x H x W,
+    float64 / float32 / uint16): krig_empirical_variogram.  Returns (sums, counts): sums a
+    device float64 tensor [2, 2L+1, 2L+1] of squared increments per lag vector (s, dy, dx),
+    counts a numpy int64 array of pair counts in the same layout; gamma = sums / (2 counts)."""
+    import numpy as np
+    import torch
+    if not slices.is_contiguous():
+        raise ValueError("slices must be contiguous")
+    n, H, W = slices.shape
+    d = VolumeDesc(H=H, W=W, n_known=n, zfactor=1, n_sub_blocks=1, half_w=0, in_dtype=dtype_code(slices.dtype),
+                   in_scale=in_scale)
+    q = max(2 * int(max_lag) + 1, 1)  # an invalid max_lag is rejected by the library
+    sums = torch.empty((2, q, q), dtype=torch.float64, device=slices.device)
+    counts = np.zeros((2, q, q), dtype=np.int64)
+    _check(lib().krig_empirical_variogram(ctypes.byref(d), ctypes.c_void_p(slices.data_ptr()), int(max_lag),
+                                          ctypes.c_void_p(sums.data_ptr()),
+                                          counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream(stream)))
+    return sums, counts
 
 
 def desc_for(slices_shape, zfactor, half_w, n_sub_blocks, dtype_code_, in_scale=1.0):
