@@ -438,12 +438,29 @@ def time_variogram(args, vol, s_dev, stream, flush, peaks, max_lag=8):
     pairs = int(counts.sum())
     out = {"value": pairs / (ms * 1e-3), "unit": "voxel pairs/s", "ms_per_call": ms, "max_lag": max_lag,
            "lag_vectors": int(counts.size), "pairs_per_call": pairs}
+    out["fit"] = variogram_fits(sums.cpu().numpy(), counts, vol)
     if peaks:
         peak = peaks["fp32_fma_gflops"] * 1e9 / 2 / 2  # FP32 instructions/s, two per pair
         out["roofline"] = {"bound": "alu", "achieved": pairs / (ms * 1e-3), "peak": peak, "unit": "pairs/s",
                            "frac": pairs / (ms * 1e-3) / peak,
                            "peak_source": "measured FP32 FMA rate / 2 instructions per pair"}
     return out
+
+
+def variogram_fits(sums, counts, vol):
+    """Weighted least-squares fit of the workload's model to the empirical variogram (distance
+    classes of the per-lag-vector sums), beside the variogram the benchmark interpolates with."""
+    from paper_2303_09523_gb300 import fit
+    res = {"model": vol.model, "used": {"nugget": vol.nugget, "sill": vol.sill, "range": vol.range}}
+    try:
+        h, gamma, n = fit.variogram_bins(sums, counts, vol.zfactor)
+        r = fit.fit_variogram_wls(h, gamma, n, vol.model)
+    except Exception as e:  # scipy missing, or no fit: the line reports it instead of failing the run
+        res["wls"] = "unavailable: %s" % e
+        return res
+    nug, sill, rng = r["theta"]
+    res["wls"] = {"nugget": nug, "sill": sill, "range": rng, "classes": int(len(h)), "max_lag_length": float(h.max())}
+    return res
 
 
 def time_batch(args, dev, stream, flush):
