@@ -280,13 +280,9 @@ def main():
     kms, klaunch = plan.get_timing()
     plan.device_status(stream)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     vox_step = vol.n_missing
-    value = vox_step * args.steps * world / (total_ms * 1e-3)
+    value = whole_job_rate(vox_step, args.steps, world, total_ms)
 
     # dominant kernel (stencil apply) roofline
     peak, peak_kind = _peaks()
@@ -319,8 +315,8 @@ def main():
         e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": vox_step * args.steps * world / (e2e_ms * 1e-3), "unit": "voxels/s",
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e = {"value": whole_job_rate(vox_step, args.steps, world, e2e_ms), "unit": "voxels/s",
            "h2d_bytes_per_step": int(s_pin.numel() * s_pin.element_size()),
            "d2h_bytes_per_step": int(out_pin.numel() * out_pin.element_size())}
 
@@ -413,6 +409,23 @@ def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
             "replay": "CUDA graph of loo_forward + backward",
             "voxels_per_step": nvox, "loss": float(loss.item()),
             "grad_theta": [float(x) for x in gp.cpu()]}
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (the job ends with it): an all-reduce (max) across the process
+    group, or x itself when there is one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step, steps, world, ms):
+    """Units per second of the whole job: every rank processes units_per_step per step (weak
+    scaling, independent replicas), all done when the slowest rank's ms have passed."""
+    return units_per_step * steps * world / (ms * 1e-3)
 
 
 def time_variogram(args, vol, s_dev, stream, flush, peaks, max_lag=8):
