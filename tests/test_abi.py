@@ -114,3 +114,26 @@ def test_calls_without_workspace_are_rejected(lib):
 def test_null_plan(lib):
     assert lib.krig_interpolate(None, None, None, None, None, None) == binding.KRIG_EINVAL
     assert lib.krig_plan_device_status(None, None) == binding.KRIG_EINVAL
+
+
+@pytest.mark.parametrize("bad,lag", [
+    (dict(), 17),                                   # lag beyond the halo the kernel stages
+    (dict(), -1),
+    (dict(H=0), 2),
+    (dict(n_known=0), 2),
+    (dict(in_dtype=7), 2),
+    (dict(in_dtype=binding.U16, in_scale=-1.0), 2),
+])
+def test_empirical_variogram_rejects_before_any_launch(lib, bad, lag):
+    d = _desc(**bad)
+    vd = binding.VolumeDesc(d["H"], d["W"], d["n_known"], d["zfactor"], d["n_sub_blocks"], d["half_w"],
+                            d["in_dtype"], d["in_scale"])
+    counts = (ctypes.c_int64 * 2)()
+    st = lib.krig_empirical_variogram(ctypes.byref(vd), ctypes.c_void_p(256), lag, ctypes.c_void_p(256), counts,
+                                      None)
+    assert st == binding.KRIG_EINVAL
+    assert len(lib.krig_last_error()) > 0
+    assert lib.krig_empirical_variogram(None, ctypes.c_void_p(256), 2, ctypes.c_void_p(256), None,
+                                        None) == binding.KRIG_EINVAL
+    assert lib.krig_empirical_variogram(ctypes.byref(vd), None, 2, ctypes.c_void_p(256), None,
+                                        None) == binding.KRIG_EINVAL
