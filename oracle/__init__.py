@@ -8,7 +8,9 @@ the CUDA library (``paper_2303_09523_gb300``) and neither imports the other.
 The arithmetic lives in ``krig_oracle.c`` (Gaussian elimination with partial
 pivoting on the bordered ordinary-kriging system, Appendix A with one constant
 predictor; sub-block layout of Algorithm 1).  This module marshals numpy arrays
-through ctypes, and holds one numpy function of its own:
+through ctypes (``krig_oracle.c`` also holds the universal-kriging solver of
+Appendix A with polynomial drift, ``uk_solve`` / ``uk_voxels``), and holds one
+numpy function of its own:
 ``empirical_variogram`` (the method-of-moments semivariogram of the known
 slices, the data the variogram of Sec. 4.1.2 is fitted to).
 """
@@ -48,6 +50,8 @@ def _load():
         lib.orc_krige_volume.argtypes = [dp, i32, i32, i32, i32, i32, i32, vp, i32, dp, dp]
         lib.orc_krige_voxels.argtypes = [dp, i32, i32, i32, i32, i32, vp, ctypes.c_int64, i64p, i32, dp, dp]
         lib.orc_loo.argtypes = [dp, i32, i32, i32, i32, i32, vp, i32, dp, dp, dp, dp]
+        lib.orc_uk_solve.argtypes = [ctypes.c_int, dp, dp, vp, ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.orc_uk_voxels.argtypes = [dp, i32, i32, i32, i32, i32, i32, i32, vp, ctypes.c_int64, i64p, dp, dp]
         lib.orc_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -129,6 +133,53 @@ def ok_solve(points, s0, values=None, grad=False, **vg):
         out["dw"] = dw
         out["dvar"] = dvar
     return out
+
+
+DRIFTS = {"constant": 0, "z": 1, "xyz": 2}
+
+
+def uk_solve(points, s0, drift="xyz", values=None, **vg):
+    """Universal kriging at ``s0`` from ``points`` (K x 3) with polynomial drift
+    ``constant`` ({1}: ordinary kriging), ``z`` ({1, z}) or ``xyz`` ({1, x, y, z})
+    (Appendix A: one unbiasedness constraint and Lagrange multiplier per predictor).
+
+    Returns dict with ``w`` (K), ``mu`` (one per predictor), ``var`` = w'gamma0 + mu'f0 and
+    ``est`` (if values given).
+    """
+    d = DRIFTS[drift] if isinstance(drift, str) else int(drift)
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    K = pts.shape[0]
+    s0 = np.ascontiguousarray(s0, dtype=np.float64)
+    vals = None if values is None else np.ascontiguousarray(values, dtype=np.float64)
+    w = np.zeros(K)
+    mu = np.zeros(4)
+    var = np.zeros(1)
+    est = np.zeros(1)
+    v = _vg(**vg)
+    st = _load().orc_uk_solve(K, _ptr(pts), _ptr(s0), ctypes.byref(v), d, _ptr(vals), _ptr(w), _ptr(mu),
+                              _ptr(var), _ptr(est))
+    _check(st, "uk_solve")
+    out = {"w": w, "mu": mu[:(1, 2, 4)[d]].copy(), "var": float(var[0])}
+    if vals is not None:
+        out["est"] = float(est[0])
+    return out
+
+
+def uk_voxels(slices, g, r, zyx, slabs=2, drift="xyz", **vg):
+    """Universal kriging estimate and variance at output voxels ``zyx`` (M x 3, output z), from
+    ``slabs`` known slices (2: the bracketing pair; 4: one more on each side where it exists),
+    window (2r+1)^2 truncated at the in-plane border; known slices copied."""
+    d = DRIFTS[drift] if isinstance(drift, str) else int(drift)
+    s = np.ascontiguousarray(slices, dtype=np.float64)
+    n, H, W = s.shape
+    idx = np.ascontiguousarray(zyx, dtype=np.int64).reshape(-1, 3)
+    est = np.empty(idx.shape[0])
+    var = np.empty(idx.shape[0])
+    v = _vg(**vg)
+    st = _load().orc_uk_voxels(_ptr(s), n, H, W, g, r, slabs, d, ctypes.byref(v), idx.shape[0],
+                               idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(est), _ptr(var))
+    _check(st, "uk_voxels")
+    return est, var
 
 
 def n_out(n, g):

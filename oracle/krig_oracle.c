@@ -472,6 +472,140 @@ int orc_loo(const double* slices, int32_t n, int32_t H, int32_t W, int32_t g, in
     return bad ? bad : ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Universal kriging / kriging with external drift (Appendix A, p > 1).      */
+/*                                                                          */
+/* The weights honour sum_i w_i q_k(s_i) = q_k(s0) for every predictor q_k    */
+/* (Appendix A's constraint), one Lagrange multiplier each, in the variogram */
+/* form                                                                     */
+/*     [ Gamma  F ] [ w  ]   [ gamma0 ]                                      */
+/*     [ F^T    0 ] [ mu ] = [ f0     ],  F_ik = q_k(s_i), f0_k = q_k(s0),    */
+/* and the kriging variance is w^T gamma0 + mu^T f0.  Predictors here are    */
+/* polynomial drifts in the coordinates (the paper names universal kriging   */
+/* without saying which): drift 0 = {1} (ordinary kriging), 1 = {1, z},      */
+/* 2 = {1, x, y, z}.                                                         */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_MAX_SLABS 4
+#define ORC_UK_MAX_K (ORC_MAX_SLABS * (2 * ORC_MAX_R + 1) * (2 * ORC_MAX_R + 1))
+
+static int drift_terms(int drift) { return drift == 0 ? 1 : (drift == 1 ? 2 : 4); }
+
+static void drift_row(int drift, const double* s, double* q)
+{
+    q[0] = 1.0;
+    if (drift == 1) {
+        q[1] = s[2];
+    } else if (drift == 2) {
+        q[1] = s[0];
+        q[2] = s[1];
+        q[3] = s[2];
+    }
+}
+
+int orc_uk_solve(int K, const double* pts, const double* s0, const orc_variogram* v, int drift,
+                 const double* vals, double* w, double* mu, double* var, double* est)
+{
+    if (K < 1 || K > ORC_UK_MAX_K || !pts || !s0 || !v || drift < 0 || drift > 2) return ORC_EINVAL;
+    const int p = drift_terms(drift), m = K + p;
+    double* A = (double*)malloc(sizeof(double) * ((size_t)m * m + 2 * (size_t)m));
+    if (!A) return ORC_ENOMEM;
+    double* B = A + (size_t)m * m;
+    double* g0 = B + m;
+    double q[4], q0[4];
+    drift_row(drift, s0, q0);
+    for (int i = 0; i < K; ++i) {
+        for (int j = 0; j < K; ++j) A[i * m + j] = orc_gamma(v, dist3(pts + 3 * i, pts + 3 * j));
+        drift_row(drift, pts + 3 * i, q);
+        for (int k = 0; k < p; ++k) {
+            A[i * m + K + k] = q[k];
+            A[(K + k) * m + i] = q[k];
+        }
+        g0[i] = orc_gamma(v, dist3(pts + 3 * i, s0));
+    }
+    for (int k = 0; k < p; ++k) {
+        for (int l = 0; l < p; ++l) A[(K + k) * m + K + l] = 0.0;
+        g0[K + k] = q0[k];
+    }
+    for (int i = 0; i < m; ++i) B[i] = g0[i];
+    int st = orc_gauss_solve(m, A, B, 1);
+    if (st != ORC_OK) { free(A); return st; }
+    double s_var = 0.0, s_est = 0.0;
+    for (int i = 0; i < m; ++i) s_var += B[i] * g0[i];  /* w^T gamma0 + mu^T f0 */
+    if (vals)
+        for (int i = 0; i < K; ++i) s_est += B[i] * vals[i];
+    if (w) for (int i = 0; i < K; ++i) w[i] = B[i];
+    if (mu) for (int k = 0; k < p; ++k) mu[k] = B[K + k];
+    if (var) *var = s_var;
+    if (est) *est = s_est;
+    free(A);
+    return ORC_OK;
+}
+
+/* Neighbourhood over `slabs` known slices (2: j, j+1; 4: j-1 .. j+2, those
+ * that exist) of a target in gap j at offset t, window (2r+1)^2 truncated at
+ * the in-plane border; coordinates relative to the target. */
+static int gather_slabs(const double* slices, int n, int H, int W, int g, int j, int t, int x, int y, int r,
+                        int slabs, double* pts, double* vals)
+{
+    const size_t plane = (size_t)H * W;
+    const int first = slabs == 4 ? j - 1 : j, last = slabs == 4 ? j + 2 : j + 1;
+    int K = 0;
+    for (int jj = first; jj <= last; ++jj) {
+        if (jj < 0 || jj >= n) continue;
+        const double dz = (double)(jj - j) * g - t;
+        for (int dy = -r; dy <= r; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -r; dx <= r; ++dx) {
+                const int xx = x + dx;
+                if (xx < 0 || xx >= W) continue;
+                pts[3 * K + 0] = (double)dx;
+                pts[3 * K + 1] = (double)dy;
+                pts[3 * K + 2] = dz;
+                vals[K] = slices[(size_t)jj * plane + (size_t)yy * W + xx];
+                ++K;
+            }
+        }
+    }
+    return K;
+}
+
+/* Universal kriging at sampled output voxels (z, y, x) of the (n-1)g+1 slice
+ * output: known slices copied, missing voxels predicted from `slabs` known
+ * slices with the given drift.  est, var: count values (var nullable). */
+int orc_uk_voxels(const double* slices, int32_t n, int32_t H, int32_t W, int32_t g, int32_t r, int32_t slabs,
+                  int32_t drift, const orc_variogram* v, int64_t count, const int64_t* zyx, double* est, double* var)
+{
+    if (!slices || !zyx || !est || !check_args(n, H, W, g, r, v) || (slabs != 2 && slabs != 4) || drift < 0 ||
+        drift > 2)
+        return ORC_EINVAL;
+    const int64_t nout = (int64_t)(n - 1) * g + 1;
+    for (int64_t i = 0; i < count; ++i)
+        if (zyx[3 * i] < 0 || zyx[3 * i] >= nout || zyx[3 * i + 1] < 0 || zyx[3 * i + 1] >= H ||
+            zyx[3 * i + 2] < 0 || zyx[3 * i + 2] >= W)
+            return ORC_EINVAL;
+    const size_t plane = (size_t)H * W;
+    int bad = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int z = (int)zyx[3 * i], y = (int)zyx[3 * i + 1], x = (int)zyx[3 * i + 2];
+        const int j = z / g, t = z % g;
+        double e, s2;
+        if (t == 0) {
+            e = slices[(size_t)j * plane + (size_t)y * W + x];
+            s2 = 0.0;
+        } else {
+            double pts[3 * ORC_UK_MAX_K], vals[ORC_UK_MAX_K];
+            const int K = gather_slabs(slices, n, H, W, g, j, t, x, y, r, slabs, pts, vals);
+            const int st = orc_uk_solve(K, pts, s0_origin, v, drift, vals, NULL, NULL, &s2, &e);
+            if (st != ORC_OK) { bad |= st; e = NAN; s2 = NAN; }
+        }
+        est[i] = e;
+        if (var) var[i] = s2;
+    }
+    return bad ? bad : ORC_OK;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -395,3 +395,120 @@ def test_empirical_variogram_constant_and_symmetry():
     # lags past the slice give no pairs
     sums, counts = oracle.empirical_variogram(np.zeros((2, 2, 3)), 3)
     assert counts[0, 3, 0] == 0 and counts[0, 3 + 2, 3] == 0 and counts[1, 3, 3] == 2 * 3
+
+
+# ---------------------------------------------------------------------------
+# universal kriging / kriging with external drift (Appendix A, p > 1)
+# ---------------------------------------------------------------------------
+_UK_VG = [dict(model="spherical", nugget=0.0, sill=1.0, range=6.0),
+          dict(model="exponential", nugget=0.05, sill=0.8, range=4.0)]
+
+
+def _uk_points(seed, K=14):
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(-3.0, 3.0, size=(K, 3))
+    s0 = rng.uniform(-1.0, 1.0, size=3)
+    return pts, s0
+
+
+@pytest.mark.parametrize("vg", _UK_VG)
+def test_uk_constant_drift_is_ordinary_kriging(vg):
+    pts, s0 = _uk_points(21)
+    vals = np.random.default_rng(22).normal(size=len(pts))
+    o = oracle.ok_solve(pts, s0, vals, **vg)
+    u = oracle.uk_solve(pts, s0, "constant", vals, **vg)
+    assert np.array_equal(o["w"], u["w"]) and o["est"] == u["est"]
+    assert u["var"] == pytest.approx(o["var"], rel=1e-13) and u["mu"][0] == pytest.approx(o["mu"], rel=1e-13)
+
+
+@pytest.mark.parametrize("vg", _UK_VG)
+def test_uk_reproduces_its_drift_and_honours_the_constraints(vg):
+    pts, s0 = _uk_points(23)
+    lin = lambda p: 1.5 + 0.7 * p[..., 0] - 0.4 * p[..., 1] + 2.1 * p[..., 2]
+    zlin = lambda p: -0.3 + 1.7 * p[..., 2]
+    u = oracle.uk_solve(pts, s0, "xyz", lin(pts), **vg)
+    assert u["est"] == pytest.approx(lin(s0), abs=1e-11)
+    F = np.column_stack([np.ones(len(pts)), pts])
+    assert np.allclose(F.T @ u["w"], np.concatenate([[1.0], s0]), atol=1e-12)
+    uz = oracle.uk_solve(pts, s0, "z", zlin(pts), **vg)
+    assert uz["est"] == pytest.approx(zlin(s0), abs=1e-11)
+    assert np.allclose(np.column_stack([np.ones(len(pts)), pts[:, 2]]).T @ uz["w"], [1.0, s0[2]], atol=1e-12)
+    # the z drift alone does not reproduce a trend in x: the drift terms matter
+    xlin = lambda p: 2.0 * p[..., 0]
+    assert abs(oracle.uk_solve(pts, s0, "z", xlin(pts), **vg)["est"] - xlin(s0)) > 1e-6
+
+
+@pytest.mark.parametrize("vg", _UK_VG)
+@pytest.mark.parametrize("drift", ["z", "xyz"])
+def test_uk_weights_minimise_the_estimation_variance(vg, drift):
+    """Under the constraints F'w = f0 (with sum w = 1), the estimation variance in the variogram
+    form is 2 w'gamma0 - w'Gamma w; the solver's weights give its minimum, equal to w'gamma0 + mu'f0,
+    and every feasible perturbation raises it."""
+    pts, s0 = _uk_points(24)
+    u = oracle.uk_solve(pts, s0, drift, None, **vg)
+    K = len(pts)
+    G = np.array([[oracle.gamma(np.linalg.norm(pts[i] - pts[j]), **vg) for j in range(K)] for i in range(K)])
+    g0 = np.array([oracle.gamma(np.linalg.norm(pts[i] - s0), **vg) for i in range(K)])
+    var = lambda w: 2.0 * w @ g0 - w @ G @ w
+    assert var(u["w"]) == pytest.approx(u["var"], rel=1e-10)
+    F = np.column_stack([np.ones(K), pts[:, 2]]) if drift == "z" else np.column_stack([np.ones(K), pts])
+    _, _, Vt = np.linalg.svd(F.T)
+    null = Vt[F.shape[1]:]  # directions with F'v = 0
+    rng = np.random.default_rng(25)
+    for _ in range(20):
+        v = null.T @ rng.normal(size=null.shape[0])
+        assert var(u["w"] + 0.05 * v) > var(u["w"])
+
+
+@pytest.mark.parametrize("slabs", [2, 4])
+def test_uk_voxels_reproduce_a_linear_volume(slabs):
+    """A stack sampled from a + b x + c y + d z (known slice j at z = j g) is reproduced at every
+    missing voxel by the {1, x, y, z} drift, including gaps at the stack ends where the 4-slice
+    neighbourhood is truncated; known slices are copied."""
+    n, H, W, g, r = 5, 7, 8, 3, 1
+    k, y, x = np.meshgrid(np.arange(n), np.arange(H), np.arange(W), indexing="ij")
+    f = lambda z, yy, xx: 0.4 + 0.11 * xx - 0.07 * yy + 0.05 * z
+    S = f(k * g, y, x)
+    zz, yy, xx = np.meshgrid(np.arange((n - 1) * g + 1), np.arange(H), np.arange(W), indexing="ij")
+    zyx = np.stack([zz.ravel(), yy.ravel(), xx.ravel()], 1)
+    est, var = oracle.uk_voxels(S, g, r, zyx, slabs=slabs, drift="xyz", model="exponential", nugget=0.02,
+                                sill=1.0, range=5.0)
+    assert np.allclose(est, f(zyx[:, 0], zyx[:, 1], zyx[:, 2]), atol=1e-10)
+    known = zyx[:, 0] % g == 0
+    assert np.all(var[known] == 0.0) and np.all(var[~known] > 0.0)
+
+
+def test_uk_voxels_constant_drift_two_slabs_is_the_ok_volume():
+    vol = np.random.default_rng(26).normal(size=(4, 9, 10))
+    g, r = 4, 1
+    rng = np.random.default_rng(27)
+    zyx = np.stack([rng.integers(0, (4 - 1) * g + 1, 300), rng.integers(0, 9, 300), rng.integers(0, 10, 300)], 1)
+    vg = dict(model="spherical", nugget=0.01, sill=1.0, range=7.0)
+    e1, v1 = oracle.uk_voxels(vol, g, r, zyx, slabs=2, drift="constant", **vg)
+    e2, v2 = oracle.krige_voxels(vol, g, r, zyx, **vg)
+    assert np.array_equal(e1, e2)
+    assert np.allclose(v1, v2, rtol=1e-12, atol=1e-15)
+
+
+def test_uk_voxels_neighbourhood_is_the_stated_slab_window():
+    """The 4-slice neighbourhood of a target in gap j at offset t: known slices j-1 .. j+2 that
+    exist, the (2r+1)^2 window around (x, y) in each, cut at the border, at dz = (jj - j) g - t;
+    the 2-slice one uses j and j+1.  Built here point by point and solved directly."""
+    n, H, W, g, r = 6, 8, 9, 3, 1
+    S = np.random.default_rng(28).normal(size=(n, H, W))
+    vg = dict(model="spherical", nugget=0.02, sill=1.0, range=6.0)
+    for slabs in (2, 4):
+        for (j, t, y, x) in [(0, 1, 0, 0), (1, 2, 4, 5), (4, 1, 7, 8), (2, 2, 3, 0)]:
+            pts, vals = [], []
+            for jj in (range(j - 1, j + 3) if slabs == 4 else range(j, j + 2)):
+                if not 0 <= jj < n:
+                    continue
+                for dy in range(-r, r + 1):
+                    for dx in range(-r, r + 1):
+                        if 0 <= y + dy < H and 0 <= x + dx < W:
+                            pts.append((dx, dy, (jj - j) * g - t))
+                            vals.append(S[jj, y + dy, x + dx])
+            ref = oracle.uk_solve(np.array(pts, float), np.zeros(3), "xyz", np.array(vals), **vg)
+            est, var = oracle.uk_voxels(S, g, r, [[j * g + t, y, x]], slabs=slabs, drift="xyz", **vg)
+            assert est[0] == pytest.approx(ref["est"], rel=1e-12, abs=1e-14)
+            assert var[0] == pytest.approx(ref["var"], rel=1e-12)
