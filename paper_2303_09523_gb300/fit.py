@@ -15,17 +15,49 @@ The classical alternative fits the model curve to the empirical variogram:
 least squares with Cressie's weights N(h) / gamma(h; theta)^2 (a three-parameter
 fit over a few dozen classes, on the host).
 """
+import json
 import math
+import os
 
 from . import binding
 
 
+def fit_log_append(path, record):
+    """Append one step of a fit as a JSON line (flushed and synced, so a crash leaves at most a
+    partial last line)."""
+    with open(path, "a") as f:
+        f.write(json.dumps(record) + "\n")
+        f.flush()
+        os.fsync(f.fileno())
+
+
+def fit_log_last(path):
+    """The last complete record of a fit log, or None (no file, or no complete line)."""
+    if not os.path.exists(path):
+        return None
+    last = None
+    with open(path) as f:
+        for line in f:
+            if not line.endswith("\n"):
+                break  # a partial last line: the step it describes did not finish
+            try:
+                last = json.loads(line)
+            except ValueError:
+                break
+    return last
+
+
 def fit_variogram_loo(slices, zfactor, half_w, n_sub_blocks, model, sill, init_range=8.0, init_ratio=0.05,
-                      steps=50, lr=0.1):
+                      steps=50, lr=0.1, log_path=None, resume=False):
     """Adam on (log range, log nugget/sill).  ``slices``: CUDA tensor (n, H, W), float32 or float64.
 
+    With ``log_path`` every step is appended there as a JSON line (step, theta, loss, the two
+    parameters and Adam's state); with ``resume=True`` the fit continues after the last complete
+    record of that log, with the same parameters and optimizer state, so an interrupted fit ends
+    where an uninterrupted one would.
+
     Returns dict: ``theta`` (nugget, sill, range) at the end, ``loss`` there, ``losses`` per step and
-    ``trajectory`` of theta per step.
+    ``trajectory`` of theta per step (the steps run by this call).
     """
     import torch
 
@@ -34,12 +66,23 @@ def fit_variogram_loo(slices, zfactor, half_w, n_sub_blocks, model, sill, init_r
                      requires_grad=True)
     opt = torch.optim.Adam([p], lr=lr)
     losses, traj = [], []
+    first = 0
+    if resume and log_path is not None:
+        rec = fit_log_last(log_path)
+        if rec is not None:
+            with torch.no_grad():
+                p.copy_(torch.tensor(rec["p"], dtype=torch.float64, device=dev))
+            st = opt.state[p]
+            st["step"] = torch.tensor(float(rec["adam"]["step"]), dtype=torch.float32)
+            st["exp_avg"] = torch.tensor(rec["adam"]["exp_avg"], dtype=torch.float64, device=dev)
+            st["exp_avg_sq"] = torch.tensor(rec["adam"]["exp_avg_sq"], dtype=torch.float64, device=dev)
+            first = int(rec["step"]) + 1
 
     def theta_of(q):
         return torch.stack([torch.exp(q[1]) * sill, torch.ones((), dtype=torch.float64, device=dev) * sill,
                             torch.exp(q[0])])
 
-    for _ in range(steps):
+    for it in range(first, steps):
         opt.zero_grad()
         th = theta_of(p)
         loss = binding.loo_loss(slices, th, zfactor, half_w, n_sub_blocks, model)
@@ -47,6 +90,13 @@ def fit_variogram_loo(slices, zfactor, half_w, n_sub_blocks, model, sill, init_r
         opt.step()
         losses.append(float(loss.detach()))
         traj.append([float(x) for x in th.detach()])
+        if log_path is not None:
+            st = opt.state[p]
+            fit_log_append(log_path, {"step": it, "theta": traj[-1], "loss": losses[-1],
+                                      "p": [float(x) for x in p.detach()],
+                                      "adam": {"step": float(st["step"]),
+                                               "exp_avg": [float(x) for x in st["exp_avg"]],
+                                               "exp_avg_sq": [float(x) for x in st["exp_avg_sq"]]}})
     with torch.no_grad():
         th = theta_of(p)
         final = float(binding.loo_loss(slices, th, zfactor, half_w, n_sub_blocks, model))

@@ -46,3 +46,32 @@ def test_variogram_bins_pool_by_rounded_length():
     h2 = (np.sqrt(len0 ** 2 + g * g) * counts[1]).sum() / n2
     assert np.allclose(n, [n1, n2]) and np.allclose(gamma, [s1 / (2 * n1), s2 / (2 * n2)])
     assert np.allclose(h, [h1, h2])
+
+
+def test_fit_log_keeps_complete_records_only(tmp_path):
+    path = str(tmp_path / "fit.jsonl")
+    assert fit.fit_log_last(path) is None
+    fit.fit_log_append(path, {"step": 0, "x": 1.5})
+    fit.fit_log_append(path, {"step": 1, "x": 2.5})
+    with open(path, "a") as f:
+        f.write('{"step": 2, "x": 3')  # interrupted mid-write
+    assert fit.fit_log_last(path) == {"step": 1, "x": 2.5}
+
+
+def test_loo_fit_resumes_exactly(tmp_path, monkeypatch):
+    """An interrupted fit resumed from its log ends with the same parameters, bit for bit, as an
+    uninterrupted one (the loss is replaced by a smooth CPU function of theta here)."""
+    torch = pytest.importorskip("torch")
+
+    def fake_loss(slices, th, zfactor, half_w, n_sub_blocks, model):
+        return (torch.log(th[2]) - 1.3) ** 2 + (torch.log(th[0] / th[1]) + 2.0) ** 2 + 0.01 * slices.sum()
+
+    monkeypatch.setattr(fit.binding, "loo_loss", fake_loss)
+    s = torch.zeros((3, 4, 4), dtype=torch.float64)
+    full = fit.fit_variogram_loo(s, 2, 1, 1, "spherical", 0.5, steps=12)
+    path = str(tmp_path / "fit.jsonl")
+    fit.fit_variogram_loo(s, 2, 1, 1, "spherical", 0.5, steps=5, log_path=path)
+    rest = fit.fit_variogram_loo(s, 2, 1, 1, "spherical", 0.5, steps=12, log_path=path, resume=True)
+    assert rest["theta"] == full["theta"]
+    assert rest["losses"] == full["losses"][5:]
+    assert fit.fit_log_last(path)["step"] == 11
