@@ -178,7 +178,7 @@ def run_reference(args, rank, world):
                          "sample": "%d random missing voxels per step of %s" % (vox // args.steps, vol.name)},
         "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
 
 
 def main():
@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--no-loo", action="store_true", help="skip the leave-one-slice-out fwd+bwd timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-volume batched graph-replay timing")
     ap.add_argument("--no-variogram", action="store_true", help="skip the empirical-variogram timing")
+    ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -361,7 +362,7 @@ def main():
             "wall_s_timed_region": t_wall,
         }
         line.update(extra)
-        print(json.dumps(line), flush=True)
+        emit(line, args)
     plan.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -409,6 +410,15 @@ def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
             "replay": "CUDA graph of loo_forward + backward",
             "voxels_per_step": nvox, "loss": float(loss.item()),
             "grad_theta": [float(x) for x in gp.cpu()]}
+
+
+def emit(line, args):
+    """The run's one JSON line on stdout, and appended to ``--results`` (JSON lines) if given."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if getattr(args, "results", None):
+        with open(args.results, "a") as f:
+            f.write(text + "\n")
 
 
 def max_over_ranks(x, dist, device):

@@ -49,3 +49,17 @@ def test_single_process_passthrough():
     import bench
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.whole_job_rate(10, 2, 1, 4.0) == pytest.approx(10 * 2 / 4e-3)
+
+
+def test_emit_appends_json_lines(tmp_path, capsys):
+    import json
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    path = str(tmp_path / "runs.jsonl")
+    for v in (1.0, 2.0):
+        bench.emit({"metric": "m", "value": v}, types.SimpleNamespace(results=path))
+    bench.emit({"metric": "m", "value": 3.0}, types.SimpleNamespace(results=None))
+    out = capsys.readouterr().out.strip().splitlines()
+    assert [json.loads(x)["value"] for x in out] == [1.0, 2.0, 3.0]
+    assert [json.loads(x)["value"] for x in open(path)] == [1.0, 2.0]
