@@ -63,3 +63,18 @@ def test_emit_appends_json_lines(tmp_path, capsys):
     out = capsys.readouterr().out.strip().splitlines()
     assert [json.loads(x)["value"] for x in out] == [1.0, 2.0, 3.0]
     assert [json.loads(x)["value"] for x in open(path)] == [1.0, 2.0]
+
+
+def test_reference_arm_runs_on_cpu():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and prints the
+    contract's JSON line (no GPU involved)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--ref-step-s", "0.2"], capture_output=True, text=True, timeout=300,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
