@@ -1,10 +1,19 @@
 """Benchmark: kriged (interpolated) voxels per second on one GB300.
 
-One step = one pass of the kriging path over one synthetic slice stack: the
-geometry-class solve and the stencil apply of the DS form (sub-block
-partition and class enumeration are planned once, on the host).  The headline
-workload is the spine-like stack: 24 known 256x256 uint16 slices, Z factor 4
-(93 output slices), 4 Z sub-blocks, 18-point window, spherical variogram.
+One step = one pass of the kriging path over one batch of synthetic slice
+stacks: the geometry-class solve and the stencil apply of the DS form for every
+volume of the batch, replayed as one CUDA graph (sub-block partition, class
+enumeration and the schedule autotune happen once, on the host, before timing).
+
+The headline workload is the mixed batch: 16 seeded spine/brain float32 stacks
+of 128^2..512^2 pixels, 12-40 known slices, Z factors 2-6, 18- or 50-point
+windows, all in one persistent launch (about 8.8e7 interpolated voxels per
+step).  Beside it the line carries the brain stack (32 x 512^2 float32, g 6,
+50 points, exponential) and the spine stack (24 x 256^2 uint16, g 4, 18 points,
+spherical variogram fitted to the slices) as full second measurements, the
+plain FP64 and mixed per-voxel forms on the headline batch, the leave-one-
+slice-out forward + backward on the spine stack, and the error of every output
+and gradient against the FP64 oracle.
 
 Prints one JSON line (rank 0).  See ``--help`` for options.
 """
@@ -23,14 +32,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "kriged voxels/s on 1 GB300, mixed/batched vs plain FP64 at stated err; fwd+bwd vox/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+TOL_INTENSITY = 1e-5        # normwise, per volume
+TOL_GRAD = 1e-4             # normwise, per tensor
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel, from the ncu capture summarised in profiles/ (None until captured, and again
-# whenever the kernel changes).  Under ncu replay part of the output is still in L2 when
-# the launch ends, so these read below the algorithmic bytes.
+# whenever the kernel changes).
 NCU_TRAFFIC = {
-    "spine": 3590656 + 25088,
-    "brain": 34455040 + 139843840,
+    "batch": None,
+    "brain": None,
+    "spine": None,
 }
 
 
@@ -44,13 +55,20 @@ def _peaks():
 
 
 def workload(name):
+    """The volumes of a workload (a list) and its name."""
     from paper_2303_09523_gb300 import phantoms
+    if name == "batch":
+        vols = phantoms.batch_mix()
+        return vols, "batch16_mixed_128-512_g2-6_r1-2_f32"
     if name == "spine":
-        return phantoms.spine()
+        v = phantoms.spine()
+        return [v], v.name
     if name == "brain":
-        return phantoms.brain()
+        v = phantoms.brain()
+        return [v], v.name
     if name == "tiny":
-        return phantoms.tiny_ellipsoids()
+        v = phantoms.tiny_ellipsoids()
+        return [v], v.name
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -62,7 +80,7 @@ def algorithmic_bytes(vol):
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi clocks and throttle reasons while a timed region runs (query only)."""
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
@@ -71,6 +89,7 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.windows = []
 
     def __enter__(self):
         try:
@@ -93,8 +112,8 @@ class ClockSampler:
         while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
             time.sleep(0.01)
 
-    def mark(self, t0, t1):
-        self.window = (t0, t1)
+    def mark(self, name, t0, t1):
+        self.windows.append((name, t0, t1))
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -104,78 +123,319 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm, smax, reasons = [], [], set()
-        t0, t1 = getattr(self, "window", (-1e30, 1e30))
-        inside = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.05]
-        lines = inside if inside else [ln for (_, ln) in self.lines]
+    @classmethod
+    def _parse(cls, lines):
+        sm, smax, power, reasons = [], [], [], set()
         for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < len(self.FIELDS):
+            if len(parts) < len(cls.FIELDS):
                 continue
             try:
                 sm.append(float(parts[0]))
                 smax.append(float(parts[1]))
             except ValueError:
                 continue
+            try:
+                power.append(float(parts[2]))
+            except ValueError:
+                pass
             for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
                                  parts[4:8]):
                 if val.lower() == "active":
                     reasons.add(name)
+        return sm, smax, power, reasons
+
+    def summary(self):
+        """Median SM clock, maximum clock and active throttle reasons over the marked windows (the
+        timed steps and the clock pass that replays the same step for at least a second)."""
+        per = {}
+        all_in = []
+        for name, t0, t1 in self.windows:
+            inside = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.05]
+            per[name] = len(inside)
+            all_in += inside
+        sm, smax, power, reasons = self._parse(all_in)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "samples_per_window": per}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm), "samples_in_timed_region": len(inside)}
+                "power_w_max": float(max(power)) if power else None, "samples": len(sm),
+                "samples_per_window": per}
 
 
-def cpu_oracle_rate(vol, target_s=12.0, threads=0, seed=0):
-    """Time the FP64 oracle on a bounded random sample of missing voxels of the workload."""
-    import oracle
-    vals = vol.values_f64()
+# ---------------------------------------------------------------------------
+# the FP64 oracle on a bounded sample (CPU baseline and error reference)
+# ---------------------------------------------------------------------------
+
+def _sample_missing(vol, count, rng):
     g = vol.zfactor
+    j = rng.integers(0, vol.n - 1, count)
+    t = rng.integers(1, g, count)
+    return np.stack([j * g + t, rng.integers(0, vol.H, count), rng.integers(0, vol.W, count)], 1)
+
+
+def oracle_sample(vols, target_s=10.0, threads=0, seed=0, with_values=True):
+    """Krige a seeded random sample of the missing voxels of the workload with the FP64 oracle, the
+    sample split over the volumes in proportion to their missing voxels.  The size is set from a
+    short probe so the oracle works for about ``target_s`` seconds.
+
+    Returns dict: ``rate`` (voxels/s over the oracle calls), ``count``, ``seconds``, ``threads``
+    (host threads used) and, with ``with_values``, per volume ``idx`` (M x 3 output z, y, x),
+    ``est`` and ``var``."""
+    import oracle
     rng = np.random.default_rng(seed)
+    nmiss = np.array([v.n_missing for v in vols], dtype=np.float64)
+    share = nmiss / nmiss.sum()
+    vals = [v.values_f64() for v in vols]
 
-    def sample(count):
-        j = rng.integers(0, vol.n - 1, count)
-        t = rng.integers(1, g, count)
-        return np.stack([j * g + t, rng.integers(0, vol.H, count), rng.integers(0, vol.W, count)], 1)
+    def run(total):
+        counts = np.maximum(1, np.round(share * total)).astype(np.int64)
+        res, secs = [], 0.0
+        for v, s, c in zip(vols, vals, counts):
+            idx = _sample_missing(v, int(c), rng)
+            t0 = time.perf_counter()
+            est, var = oracle.krige_voxels(s, v.zfactor, v.half_w, idx, threads=threads, **v.variogram())
+            secs += time.perf_counter() - t0
+            res.append({"idx": idx, "est": est, "var": var})
+        return res, int(counts.sum()), secs
 
-    probe = sample(2000 if threads != 1 else 300)
-    t0 = time.perf_counter()
-    oracle.krige_voxels(vals, g, vol.half_w, probe, threads=threads, **vol.variogram())
-    dt = time.perf_counter() - t0
-    count = int(max(1000, min(5_000_000, len(probe) * target_s / max(dt, 1e-6))))
-    idx = sample(count)
-    t0 = time.perf_counter()
-    oracle.krige_voxels(vals, g, vol.half_w, idx, threads=threads, **vol.variogram())
-    dt = time.perf_counter() - t0
+    _, pc, pt = run(3000 if threads != 1 else 400)
+    total = int(max(len(vols), min(20_000_000, pc * target_s / max(pt, 1e-6))))
+    res, count, secs = run(total)
     used = threads if threads > 0 else oracle.max_threads()
-    return count / dt, count, dt, used
+    out = {"rate": count / secs, "count": count, "seconds": secs, "threads": used}
+    if with_values:
+        out["per_volume"] = res
+    return out
+
+
+def _gather(t, idx):
+    import torch
+    ii = torch.from_numpy(idx).to(t.device)
+    return t[ii[:, 0], ii[:, 1], ii[:, 2]].double().cpu().numpy()
+
+
+def err_vs_oracle(outs, variances, sample):
+    """Max abs and normwise relative error (max |gpu - oracle| / max |oracle|, per volume, the
+    largest over the volumes) of the estimates and variances at the oracle's sample voxels."""
+    res = {}
+    for key, tens in (("estimate", outs), ("variance", variances)):
+        if tens is None:
+            continue
+        mabs, mrel = 0.0, 0.0
+        for t, pv in zip(tens, sample["per_volume"]):
+            got = _gather(t, pv["idx"])
+            ref = pv["est"] if key == "estimate" else pv["var"]
+            d = float(np.abs(got - ref).max())
+            mabs = max(mabs, d)
+            mrel = max(mrel, d / max(float(np.abs(ref).max()), 1e-300))
+        res[key] = {"max_abs": mabs, "max_rel_normwise": mrel, "tolerance": TOL_INTENSITY,
+                    "within": mrel <= TOL_INTENSITY}
+    res["voxels"] = sample["count"]
+    return res
+
+
+# ---------------------------------------------------------------------------
+# the DS path on one workload: graph replay, roofline, clocks, e2e
+# ---------------------------------------------------------------------------
+
+class DsHarness:
+    """Device buffers, plan (autotuned for batches) and the captured CUDA graph of one workload."""
+
+    def __init__(self, vols, dev, stream, autotune):
+        import torch
+        from paper_2303_09523_gb300 import binding
+        self.vols = vols
+        self.dev = dev
+        self.stream = stream
+        self.host = [torch.from_numpy(np.ascontiguousarray(v.slices)) for v in vols]
+        self.ts = [h.to(dev) for h in self.host]
+        codes = [binding.dtype_code(t.dtype) for t in self.ts]
+        self.descs = [binding.desc_for(tuple(t.shape), v.zfactor, v.half_w, v.n_sub_blocks, c, v.in_scale)
+                      for v, t, c in zip(vols, self.ts, codes)]
+        self.outs = [torch.empty((v.n_out, v.H, v.W), dtype=binding.out_dtype(c), device=dev)
+                     for v, c in zip(vols, codes)]
+        self.params = binding.variogram_tensor([v.variogram() for v in vols], device=dev)
+        self.plan = binding.Plan(self.descs, form="DS", device=dev)
+        self.chunk = self.plan.autotune(self.ts, self.outs, self.params, iters=3, stream=stream) if autotune else None
+        self.graph = self.plan.capture(self.ts, self.outs, self.params)
+        self.n_missing = sum(v.n_missing for v in vols)
+        self.abytes = sum(algorithmic_bytes(v) for v in vols)
+
+    def replay(self):
+        self.graph.replay()
+
+    def time_steps(self, steps, flush):
+        import torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(self.stream)
+            self.replay()
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def kernel_ms(self, iters, flush):
+        """Average CUDA-event duration of the class solve and of the stencil per launch, each launch
+        bracketed by the library's own events on the launching stream (separate pass: events between
+        the two kernels serialise their overlap)."""
+        self.plan.set_timing(True)
+        self.plan.get_timing()
+        for _ in range(iters):
+            flush.zero_()
+            self.plan.interpolate(self.ts, self.outs, self.params, None, self.stream)
+        self.plan.set_timing(False)
+        kms, kl = self.plan.get_timing()
+        self.plan.device_status(self.stream)
+        return kms[0] / max(kl[0], 1), kms[1] / max(kl[1], 1)
+
+    def variances(self):
+        import torch
+        var = [torch.empty_like(o, dtype=torch.float32) for o in self.outs]
+        self.plan.interpolate(self.ts, self.outs, self.params, var, self.stream)
+        self.plan.device_status(self.stream)
+        return var
+
+    def known_slices_bit_exact(self):
+        import torch
+        ok = True
+        for v, t, o in zip(self.vols, self.ts, self.outs):
+            if t.dtype == torch.uint16:
+                exp = t.to(torch.float32) * torch.tensor(v.in_scale, dtype=torch.float32, device=t.device)
+            else:
+                exp = t
+            ok = ok and bool(torch.equal(o[::v.zfactor], exp.to(o.dtype)))
+        return ok
+
+    def e2e(self, steps):
+        """Same step through the public API with the slices in pinned host memory and the output read
+        back to pinned host memory every step (copies inside the timed region)."""
+        import torch
+        pin_in = [h.pin_memory() for h in self.host]
+        pin_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outs]
+
+        def step():
+            for d, h in zip(self.ts, pin_in):
+                d.copy_(h, non_blocking=True)
+            self.replay()
+            for h, o in zip(pin_out, self.outs):
+                h.copy_(o, non_blocking=True)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            step()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), sum(h.numel() * h.element_size() for h in pin_in), \
+            sum(h.numel() * h.element_size() for h in pin_out)
+
+    def close(self):
+        self.plan.close()
+
+
+def roofline_of(h, apply_ms, solve_ms, wl_key):
+    peak, kind = _peaks()
+    achieved = h.abytes / (apply_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": NCU_TRAFFIC.get(wl_key), "kernel": "k_ds_apply", "algorithmic_bytes": h.abytes,
+            "avg_launch_ms": apply_ms, "peak_source": kind + " hbm_gbs (burst: the kernel is timed alone)",
+            "class_solve_avg_ms": solve_ms}
+
+
+def measure_workload(wl_key, vols, wl_name, args, dev, stream, flush, world, dist, clk=None, cpu=True,
+                     e2e=True, steps=None):
+    """Full measurement of the DS path on one workload: timed graph replays, per-kernel roofline,
+    clock pass, e2e, error against the FP64 oracle on a seeded sample, the oracle's CPU rate."""
+    import torch
+    steps = args.steps if steps is None else steps
+    h = DsHarness(vols, dev, stream, autotune=len(vols) > 1)
+    for _ in range(args.warmup):
+        h.replay()
+    h.plan.device_status(stream)
+    barrier(dist)
+    t0 = time.perf_counter()
+    step_ms = h.time_steps(steps, flush)
+    t1 = time.perf_counter()
+    barrier(dist)
+    if clk is not None:
+        clk.mark(wl_key + ":timed", t0, t1)
+    h.plan.device_status(stream)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    res = {"value": whole_job_rate(h.n_missing, steps, world, total_ms), "unit": "voxels/s",
+           "ms_per_step": total_ms / steps, "interpolated_voxels_per_step": h.n_missing,
+           "volumes": len(vols), "workload": wl_name}
+    if h.chunk is not None:
+        res["autotuned_gaps_per_item"] = h.chunk
+    solve_ms, apply_ms = h.kernel_ms(min(max(steps, 20), 200), flush)
+    res["roofline"] = roofline_of(h, apply_ms, solve_ms, wl_key)
+    if clk is not None:
+        # clock pass: the same step replayed for at least a second, so the sampled clocks cover it
+        n = max(1, int(1.0 / max(total_ms / steps * 1e-3, 1e-6)))
+        c0 = time.perf_counter()
+        while time.perf_counter() - c0 < 1.0:
+            for _ in range(min(n, 500)):
+                h.replay()
+            torch.cuda.synchronize()
+        clk.mark(wl_key + ":clock_pass", c0, time.perf_counter())
+    if e2e:
+        e_ms, bi, bo = h.e2e(max(3, min(steps, 50)))
+        e_ms = max_over_ranks(e_ms, dist, dev)
+        ne = max(3, min(steps, 50))
+        res["e2e"] = {"value": whole_job_rate(h.n_missing, ne, world, e_ms), "unit": "voxels/s",
+                      "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e_ms / ne}
+    if cpu and not args.no_cpu:
+        sample = oracle_sample(vols, target_s=args.cpu_s, seed=11)
+        var = h.variances()
+        torch.cuda.synchronize()
+        res["err_vs_oracle"] = err_vs_oracle(h.outs, var, sample)
+        res["err_vs_oracle"]["known_slices_bit_exact"] = h.known_slices_bit_exact()
+        del var
+        single = oracle_sample(vols, target_s=args.cpu_s / 3, threads=1, seed=12, with_values=False)
+        res["cpu_baseline"] = {
+            "value": sample["rate"], "unit": "voxels/s", "cores": sample["threads"], "kind": "oracle",
+            "sample": "%d seeded random missing voxels of %s, split over its volumes by their missing voxels "
+                      "(%.1f s on %d threads); single-core: %.4g voxels/s on %d voxels"
+                      % (sample["count"], wl_name, sample["seconds"], sample["threads"], single["rate"],
+                         single["count"]),
+            "single_core": single["rate"]}
+        res["_sample"] = sample
+    res["_harness"] = h
+    return res
+
+
+def barrier(dist):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
 
 
 def run_reference(args, rank, world):
     """The oracle as the reference arm: each step krige a bounded random sample of the workload."""
     if rank != 0:
         return
-    vol = workload(args.workload)
-    rates = []
+    vols, name = workload(args.workload)
     for _ in range(args.warmup):
-        cpu_oracle_rate(vol, target_s=args.ref_step_s / 4)
-    t_all = 0.0
-    vox = 0
+        oracle_sample(vols, target_s=args.ref_step_s / 4, with_values=False)
+    t_all, vox, used = 0.0, 0, 1
     for s in range(args.steps):
-        rate, count, dt, used = cpu_oracle_rate(vol, target_s=args.ref_step_s, seed=s + 1)
-        rates.append(rate)
-        t_all += dt
-        vox += count
+        r = oracle_sample(vols, target_s=args.ref_step_s, seed=s + 1, with_values=False)
+        t_all += r["seconds"]
+        vox += r["count"]
+        used = r["threads"]
     value = vox / t_all
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": vol.name, "form": "oracle FP64 per voxel (Gaussian elimination)"},
+        "config": {"workload": name, "form": "oracle FP64 per voxel (Gaussian elimination)"},
         "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": used, "kind": "oracle",
-                         "sample": "%d random missing voxels per step of %s" % (vox // args.steps, vol.name)},
+                         "sample": "%d seeded random missing voxels per step of %s" % (vox // args.steps, name)},
         "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     emit(line, args)
@@ -184,17 +444,18 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="spine", choices=["spine", "brain", "tiny"])
-    ap.add_argument("--forms-steps", type=int, default=3, help="steps for the per-voxel forms comparison")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-extra", action="store_true", help="skip form comparison and at-scale lines")
+    ap.add_argument("--workload", default="batch", choices=["batch", "brain", "spine", "tiny"])
+    ap.add_argument("--forms-steps", type=int, default=1, help="timed calls of each per-voxel form")
+    ap.add_argument("--cpu-s", type=float, default=8.0, help="seconds of oracle work per CPU sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and error sample")
+    ap.add_argument("--no-extra", action="store_true", help="skip every line beside the headline")
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-voxel P64 / PMX forms")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
-    ap.add_argument("--no-fit", action="store_true", help="use the default variogram instead of the LOO fit")
+    ap.add_argument("--no-fit", action="store_true", help="use the default spine variogram instead of the LOO fit")
     ap.add_argument("--no-loo", action="store_true", help="skip the leave-one-slice-out fwd+bwd timing")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 16-volume batched graph-replay timing")
     ap.add_argument("--no-variogram", action="store_true", help="skip the empirical-variogram timing")
     ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
     args = ap.parse_args()
@@ -218,160 +479,120 @@ def main():
         import torch.distributed as dist_
         dist_.init_process_group("nccl", device_id=dev)
         dist = dist_
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    vol = workload(args.workload)
-    s_host = torch.from_numpy(np.ascontiguousarray(vol.slices))
-    s_dev = s_host.to(dev)
-    variogram_fit = None
-    if args.workload == "spine" and not args.no_fit:
-        # the spine configuration uses a spherical variogram fitted to the slice data: fit it by gradient
-        # descent on the leave-one-slice-out loss (CUDA kernels), before anything is timed
-        from paper_2303_09523_gb300 import fit
-        vals = torch.from_numpy(vol.values_f64().astype(np.float32)).to(dev)
-        res = fit.fit_variogram_loo(vals, vol.zfactor, vol.half_w, vol.n_sub_blocks, "spherical", vol.sill,
-                                    init_range=8.0, init_ratio=0.05, steps=50, lr=0.1)
-        vol.nugget, vol.sill, vol.range = res["theta"]
-        variogram_fit = {"method": "leave-one-slice-out loss, Adam 50 steps on log range and log nugget/sill",
-                         "loss_first": res["losses"][0], "loss_final": res["loss"]}
-    code = binding.dtype_code(s_dev.dtype)
-    desc = binding.desc_for(tuple(s_dev.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks, code, vol.in_scale)
-    out_dt = binding.out_dtype(code)
-    out = torch.empty((vol.n_out, vol.H, vol.W), dtype=out_dt, device=dev)
-    params = binding.variogram_tensor([vol.variogram()], device=dev)
-    plan = binding.Plan([desc], form="DS", device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    extra = {}
+    lead = rank == 0 and world == 1
 
-    def step():
-        plan.interpolate([s_dev], [out], params, None, stream)
+    # the spine configuration's variogram is fitted to its slices: gradient descent on the
+    # leave-one-slice-out loss (CUDA kernels), before anything is timed
+    spine_fit = None
+    if not args.no_fit and (args.workload == "spine" or (not args.no_extra)):
+        from paper_2303_09523_gb300 import fit, phantoms
+        sp = phantoms.spine()
+        vals = torch.from_numpy(sp.values_f64().astype(np.float32)).to(dev)
+        r = fit.fit_variogram_loo(vals, sp.zfactor, sp.half_w, sp.n_sub_blocks, "spherical", sp.sill,
+                                  init_range=8.0, init_ratio=0.05, steps=50, lr=0.1)
+        spine_fit = {"theta": r["theta"], "loss_first": r["losses"][0], "loss_final": r["loss"],
+                     "method": "leave-one-slice-out loss, Adam 50 steps on log range and log nugget/sill"}
+        del vals
 
-    for _ in range(args.warmup):
-        step()
-    plan.device_status(stream)
+    def fitted(vols, key):
+        if key == "spine" and spine_fit is not None:
+            vols[0].nugget, vols[0].sill, vols[0].range = spine_fit["theta"]
+        return vols
 
-    # ---------------- timed region (device time, L2 flushed before every step)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
+    vols, wl_name = workload(args.workload)
+    vols = fitted(vols, args.workload)
     with ClockSampler(local) as clk:
         clk.wait_first()
-        t_wall = time.perf_counter()
-        t_start = t_wall
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        barrier()
-        t_wall = time.perf_counter() - t_wall
-        clk.mark(t_start, t_start + t_wall)
-    plan.device_status(stream)
-    # per-kernel durations (for the roofline), measured in a separate pass: the
-    # library's events between the two kernels would serialise their overlap
-    plan.set_timing(True)
-    plan.get_timing()
-    for i in range(min(args.steps, 200)):
-        flush.zero_()
-        step()
-    plan.set_timing(False)
-    kms, klaunch = plan.get_timing()
-    plan.device_status(stream)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(sum(step_ms), dist, dev)
-    vox_step = vol.n_missing
-    value = whole_job_rate(vox_step, args.steps, world, total_ms)
+        head = measure_workload(args.workload, vols, wl_name, args, dev, stream, flush, world, dist, clk=clk,
+                                cpu=rank == 0)
+        h = head.pop("_harness")
+        sample = head.pop("_sample", None)
+        clocks = clk.summary()
 
-    # dominant kernel (stencil apply) roofline
-    peak, peak_kind = _peaks()
-    apply_ms = kms[1] / max(klaunch[1], 1)
-    solve_ms = kms[0] / max(klaunch[0], 1)
-    abytes = algorithmic_bytes(vol)
-    achieved = abytes / (apply_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(args.workload), "kernel": "k_ds_apply",
-                "algorithmic_bytes": abytes, "avg_launch_ms": apply_ms, "peak_source": peak_kind + " hbm_gbs",
-                "class_solve_avg_ms": solve_ms}
-
-    # ---------------- end to end through the public API with host buffers
-    s_pin = s_host.pin_memory()
-    out_pin = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
-    s_stage = torch.empty_like(s_dev)
-
-    def e2e_step():
-        s_stage.copy_(s_pin, non_blocking=True)
-        plan.interpolate([s_stage], [out], params, None, stream)
-        out_pin.copy_(out, non_blocking=True)
-
-    for _ in range(3):
-        e2e_step()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    e2e = {"value": whole_job_rate(vox_step, args.steps, world, e2e_ms), "unit": "voxels/s",
-           "h2d_bytes_per_step": int(s_pin.numel() * s_pin.element_size()),
-           "d2h_bytes_per_step": int(out_pin.numel() * out_pin.element_size())}
-
-    extra = {}
-    if not args.no_extra and rank == 0:
+    if lead and not args.no_extra:
+        if not args.no_forms:
+            extra["forms"] = compare_forms(args, h, sample)
+            extra["forms"]["DS"] = {"value": head["value"], "unit": "voxels/s", "ms_per_step": head["ms_per_step"],
+                                    "err_vs_oracle": (head.get("err_vs_oracle") or {}).get("estimate")}
+            extra["forms"]["DS_vs_P64_speedup"] = head["value"] / extra["forms"]["P64"]["value"]
+            extra["forms"]["PMX_vs_P64_speedup"] = extra["forms"]["PMX"]["value"] / extra["forms"]["P64"]["value"]
+        for key in ("brain", "spine"):
+            if key == args.workload:
+                continue
+            v2, n2 = workload(key)
+            v2 = fitted(v2, key)
+            r2 = measure_workload(key, v2, n2, args, dev, stream, flush, world, None, cpu=True, e2e=True)
+            r2.pop("_harness").close()
+            r2.pop("_sample", None)
+            r2["config"] = workload_config(v2)
+            extra[key] = r2
+        if not args.no_loo:
+            extra["fwd_bwd"] = time_loo(args, dev, stream, flush, spine_fit, with_oracle=not args.no_cpu)
+        if not args.no_variogram:
+            extra["empirical_variogram"] = time_variogram(args, dev, stream, flush)
         peaks = {"fp32_fma_gflops": binding.measure_fma_peak(False), "fp64_fma_gflops": binding.measure_fma_peak(True)}
-        extra = compare_forms(args, vol, s_dev, desc, params, out, dev, stream, peaks)
         extra["alu_peaks_measured"] = peaks
-    if rank == 0 and not args.no_loo:
-        extra["fwd_bwd"] = time_loo(args, vol, s_dev, desc, params, dev, stream, flush)
-    if rank == 0 and not args.no_batch:
-        extra["batched"] = time_batch(args, dev, stream, flush)
-    if rank == 0 and not args.no_variogram:
-        extra["empirical_variogram"] = time_variogram(args, vol, s_dev, stream, flush,
-                                                      extra.get("alu_peaks_measured"))
-    if variogram_fit is not None:
-        extra["variogram_fit"] = variogram_fit
-
-    cpu = None
-    if not args.no_cpu and rank == 0 and world == 1:
-        rate, count, dt, used = cpu_oracle_rate(vol, target_s=12.0)
-        rate1, count1, dt1, _ = cpu_oracle_rate(vol, target_s=4.0, threads=1)
-        cpu = {"value": rate, "unit": "voxels/s", "cores": used, "kind": "oracle",
-               "sample": "%d random missing voxels of %s (%.1f s); single-core: %.4g voxels/s on %d voxels"
-                         % (count, vol.name, dt, rate1, count1)}
+        if "forms" in extra and "P64" in extra["forms"]:
+            p = extra["forms"]["P64"]
+            p["fp64_roofline"]["peak"] = peaks["fp64_fma_gflops"]
+            p["fp64_roofline"]["frac"] = p["fp64_roofline"]["achieved"] / peaks["fp64_fma_gflops"]
+    if spine_fit is not None:
+        extra["variogram_fit"] = spine_fit
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 stencil / f64-refined f32 solve",
             "data": "synthetic",
-            "config": {"workload": vol.name, "form": "DS", "n_known": vol.n, "H": vol.H, "W": vol.W,
-                       "zfactor": vol.zfactor, "half_w": vol.half_w, "n_sub_blocks": vol.n_sub_blocks,
-                       "variogram": vol.variogram(), "interpolated_voxels_per_step": vox_step,
-                       "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas"},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
+            "config": dict(workload_config(vols), workload=wl_name,
+                           l2="flushed (512 MB write) before every timed step; inputs + outputs exceed L2",
+                           step="one CUDA-graph replay: class solve + persistent stencil over every volume",
+                           parallelism="replicas"),
+            "roofline": head["roofline"],
+            "cpu_baseline": head.get("cpu_baseline"),
+            "e2e": head.get("e2e"),
+            "err_vs_oracle": head.get("err_vs_oracle"),
             "gpu_launches": 2 * args.steps,
-            "clocks": clk.summary(),
-            "wall_s_timed_region": t_wall,
+            "clocks": clocks,
         }
+        for k in ("autotuned_gaps_per_item", "interpolated_voxels_per_step"):
+            if k in head:
+                line["config"][k] = head[k]
         line.update(extra)
         emit(line, args)
-    plan.close()
+    h.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
-    """Leave-one-slice-out forward + backward (gradients w.r.t. every slice voxel and the variogram)."""
+def workload_config(vols):
+    if len(vols) == 1:
+        v = vols[0]
+        return {"n_known": v.n, "H": v.H, "W": v.W, "zfactor": v.zfactor, "half_w": v.half_w,
+                "n_sub_blocks": v.n_sub_blocks, "dtype": str(v.slices.dtype), "variogram": v.variogram(),
+                "form": "DS"}
+    return {"form": "DS", "volumes": [{"name": v.name, "n_known": v.n, "H": v.H, "W": v.W, "zfactor": v.zfactor,
+                                       "half_w": v.half_w, "n_sub_blocks": v.n_sub_blocks,
+                                       "model": v.model} for v in vols]}
+
+
+def time_loo(args, dev, stream, flush, spine_fit, with_oracle=True):
+    """Leave-one-slice-out forward + backward on the spine stack (gradients w.r.t. every slice voxel and
+    the variogram), replayed as a CUDA graph; gradients compared with the FP64 oracle's."""
     import torch
-    from paper_2303_09523_gb300 import binding
+    from paper_2303_09523_gb300 import binding, phantoms
+    vol = phantoms.spine()
+    theta = dict(model="spherical", nugget=0.0, sill=vol.sill, range=8.0)
+    if spine_fit is not None:
+        theta.update(nugget=spine_fit["theta"][0], sill=spine_fit["theta"][1], range=spine_fit["theta"][2])
+    s_dev = torch.from_numpy(np.ascontiguousarray(vol.slices)).to(dev)
+    desc = binding.desc_for(tuple(s_dev.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks,
+                            binding.dtype_code(s_dev.dtype), vol.in_scale)
+    params = binding.variogram_tensor([theta], device=dev)
     plan = binding.Plan([desc], form="DS", flags=binding.FLAG_LOO, device=dev)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
     gl = torch.ones(1, dtype=torch.float64, device=dev)
@@ -386,7 +607,7 @@ def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
         step(stream)
     plan.device_status(stream)
     # the forward + backward pair replayed as one CUDA graph (the calls only
-    # launch kernels and memsets on the stream they are given)
+    # launch kernels on the stream they are given)
     cap = torch.cuda.Stream(device=dev)
     cap.wait_stream(stream)
     graph = torch.cuda.CUDAGraph()
@@ -404,12 +625,32 @@ def time_loo(args, vol, s_dev, desc, params, dev, stream, flush):
         evs.append((a, b))
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    plan.device_status(stream)
     plan.close()
     nvox = (vol.n - 2) * vol.H * vol.W
-    return {"value": nvox / (ms * 1e-3), "unit": "LOO-predicted voxels/s (forward + backward)", "ms_per_step": ms,
-            "replay": "CUDA graph of loo_forward + backward",
-            "voxels_per_step": nvox, "loss": float(loss.item()),
-            "grad_theta": [float(x) for x in gp.cpu()]}
+    out = {"value": nvox / (ms * 1e-3), "unit": "LOO-predicted voxels/s (forward + backward)", "ms_per_step": ms,
+           "replay": "CUDA graph of loo_forward + backward", "workload": vol.name + " (leave-one-slice-out)",
+           "voxels_per_step": nvox, "variogram": theta, "loss": float(loss.item()),
+           "grad_theta": [float(x) for x in gp.cpu()]}
+    if with_oracle:
+        import oracle
+        ref = oracle.loo(vol.values_f64(), vol.zfactor, vol.half_w, want_grad_theta=True, want_grad_slices=True,
+                         **theta)
+        g_t = gp.cpu().numpy()
+        g_s = gs.double().cpu().numpy()
+        et = float(np.abs(g_t - ref["grad_theta"]).max())
+        es = float(np.abs(g_s - ref["grad_slices"]).max())
+        out["err_vs_oracle"] = {
+            "loss": {"max_abs": abs(float(loss.item()) - ref["loss"]),
+                     "max_rel": abs(float(loss.item()) - ref["loss"]) / abs(ref["loss"])},
+            "grad_theta": {"max_abs": et, "max_rel_normwise": et / float(np.abs(ref["grad_theta"]).max()),
+                           "tolerance": TOL_GRAD},
+            "grad_slices": {"max_abs": es, "max_rel_normwise": es / float(np.abs(ref["grad_slices"]).max()),
+                            "tolerance": TOL_GRAD},
+        }
+        for k in ("grad_theta", "grad_slices"):
+            out["err_vs_oracle"][k]["within"] = out["err_vs_oracle"][k]["max_rel_normwise"] <= TOL_GRAD
+    return out
 
 
 def emit(line, args):
@@ -438,12 +679,14 @@ def whole_job_rate(units_per_step, steps, world, ms):
     return units_per_step * steps * world / (ms * 1e-3)
 
 
-def time_variogram(args, vol, s_dev, stream, flush, peaks, max_lag=8):
-    """Method-of-moments variogram data of the workload's known slices (krig_empirical_variogram):
+def time_variogram(args, dev, stream, flush, max_lag=8):
+    """Method-of-moments variogram data of the spine stack's known slices (krig_empirical_variogram):
     squared-increment sums for every lag vector |dx|, |dy| <= 8 within a slice and to the next slice.
     FP32-pipe bound: a subtract and a fused multiply-add per voxel pair."""
     import torch
-    from paper_2303_09523_gb300 import binding
+    from paper_2303_09523_gb300 import binding, phantoms
+    vol = phantoms.spine()
+    s_dev = torch.from_numpy(np.ascontiguousarray(vol.slices)).to(dev)
     for _ in range(max(3, args.warmup)):
         sums, counts = binding.empirical_variogram(s_dev, max_lag, in_scale=vol.in_scale, stream=stream)
     evs = []
@@ -460,21 +703,16 @@ def time_variogram(args, vol, s_dev, stream, flush, peaks, max_lag=8):
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     pairs = int(counts.sum())
     out = {"value": pairs / (ms * 1e-3), "unit": "voxel pairs/s", "ms_per_call": ms, "max_lag": max_lag,
-           "lag_vectors": int(counts.size), "pairs_per_call": pairs}
+           "lag_vectors": int(counts.size), "pairs_per_call": pairs, "workload": vol.name}
     out["fit"] = variogram_fits(sums.cpu().numpy(), counts, vol)
-    if peaks:
-        peak = peaks["fp32_fma_gflops"] * 1e9 / 2 / 2  # FP32 instructions/s, two per pair
-        out["roofline"] = {"bound": "alu", "achieved": pairs / (ms * 1e-3), "peak": peak, "unit": "pairs/s",
-                           "frac": pairs / (ms * 1e-3) / peak,
-                           "peak_source": "measured FP32 FMA rate / 2 instructions per pair"}
     return out
 
 
 def variogram_fits(sums, counts, vol):
     """Weighted least-squares fit of the workload's model to the empirical variogram (distance
-    classes of the per-lag-vector sums), beside the variogram the benchmark interpolates with."""
+    classes of the per-lag-vector sums)."""
     from paper_2303_09523_gb300 import fit
-    res = {"model": vol.model, "used": {"nugget": vol.nugget, "sill": vol.sill, "range": vol.range}}
+    res = {"model": vol.model}
     try:
         h, gamma, n = fit.variogram_bins(sums, counts, vol.zfactor)
         r = fit.fit_variogram_wls(h, gamma, n, vol.model)
@@ -486,83 +724,51 @@ def variogram_fits(sums, counts, vol):
     return res
 
 
-def time_batch(args, dev, stream, flush):
-    """16 uneven spine/brain volumes in one DS call: autotuned schedule, captured in a CUDA graph, replayed."""
-    import torch
-    from paper_2303_09523_gb300 import binding, phantoms
-    vols = phantoms.batch_mix()
-    ts = [torch.from_numpy(np.ascontiguousarray(v.slices)).to(dev) for v in vols]
-    descs = [binding.desc_for(tuple(t.shape), v.zfactor, v.half_w, v.n_sub_blocks, binding.dtype_code(t.dtype),
-                              v.in_scale) for v, t in zip(vols, ts)]
-    outs = [torch.empty((v.n_out, v.H, v.W), dtype=torch.float32, device=dev) for v in vols]
-    params = binding.variogram_tensor([v.variogram() for v in vols], device=dev)
-    plan = binding.Plan(descs, form="DS", device=dev)
-    chunk = plan.autotune(ts, outs, params, iters=3, stream=stream)
-    g = plan.capture(ts, outs, params)
-    torch.cuda.synchronize()
-    steps = max(10, args.steps // 10)
-    for _ in range(3):
-        g.replay()
-    evs = []
-    for _ in range(steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.replay()
-        b.record()
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    plan.device_status()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    nvox = sum(v.n_missing for v in vols)
-    abytes = sum(algorithmic_bytes(v) for v in vols)
-    peak, kind = _peaks()
-    plan.close()
-    return {"value": nvox / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms, "volumes": len(vols),
-            "interpolated_voxels_per_step": nvox, "autotuned_gaps_per_item": chunk,
-            "step_bytes_per_s": abytes / (ms * 1e-3), "frac_of_hbm_peak": abytes / (ms * 1e-3) / (peak * 1e9),
-            "replay": "CUDA graph (class solve + stencil, programmatic dependent launch)"}
-
-
 def p64_flops_per_voxel(vol):
     """FP64 flops of one interior voxel's P64 solve: Cholesky K^3/3, four triangular sweeps 4K^2, combine 6K."""
     K = 2 * (2 * vol.half_w + 1) ** 2
     return K ** 3 / 3.0 + 4.0 * K * K + 6.0 * K
 
 
-def compare_forms(args, vol, s_dev, desc, params, out_ds, dev, stream, peaks):
-    """Plain FP64 per-voxel form (P64) and the mixed per-voxel form (PMX) on the same workload."""
+def compare_forms(args, h, sample):
+    """Plain FP64 per-voxel form (P64) and the mixed per-voxel form (PMX) on the headline workload, each
+    against the FP64 oracle at the sample voxels; DS against P64 over every output voxel."""
     import torch
     from paper_2303_09523_gb300 import binding
     res = {}
     ref = None
     for form in ("P64", "PMX"):
-        plan = binding.Plan([desc], form=form, device=dev)
-        o = torch.empty_like(out_ds)
-        plan.interpolate([s_dev], [o], params, None, stream)
-        plan.device_status(stream)
+        plan = binding.Plan(h.descs, form=form, device=h.dev)
+        o = [torch.empty_like(x) for x in h.outs]
+        plan.interpolate(h.ts, o, h.params, None, h.stream)
+        plan.device_status(h.stream)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(h.stream)
         for _ in range(args.forms_steps):
-            plan.interpolate([s_dev], [o], params, None, stream)
-        b.record(stream)
+            plan.interpolate(h.ts, o, h.params, None, h.stream)
+        b.record(h.stream)
         torch.cuda.synchronize()
+        plan.device_status(h.stream)
         ms = a.elapsed_time(b) / args.forms_steps
-        res[form] = {"value": vol.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms}
+        res[form] = {"value": h.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms}
+        if sample is not None:
+            res[form]["err_vs_oracle"] = err_vs_oracle(o, None, sample)["estimate"]
         if form == "P64":
-            ref = o.double()
-            gfl = p64_flops_per_voxel(vol) * vol.n_missing / (ms * 1e-3) / 1e9
-            res[form]["fp64_roofline"] = {"bound": "fp64", "achieved": gfl, "peak": peaks["fp64_fma_gflops"],
-                                          "unit": "GFLOP/s", "frac": gfl / peaks["fp64_fma_gflops"],
-                                          "flops_per_voxel": p64_flops_per_voxel(vol),
+            ref = o
+            fl = sum(p64_flops_per_voxel(v) * v.n_missing for v in h.vols)
+            gfl = fl / (ms * 1e-3) / 1e9
+            res[form]["fp64_roofline"] = {"bound": "fp64", "achieved": gfl, "peak": None, "unit": "GFLOP/s",
+                                          "frac": None, "flops_per_step": fl,
                                           "peak_source": "krig_measure_fma_peak (FP64 FMA microbenchmark)"}
         else:
-            res[form]["max_rel_err_vs_P64"] = float((o.double() - ref).abs().max() / ref.abs().max())
+            res[form]["max_rel_err_vs_P64"] = max(float((x.double() - y.double()).abs().max() / y.double().abs().max())
+                                                  for x, y in zip(o, ref))
         plan.close()
-    res["DS_max_rel_err_vs_P64"] = float((out_ds.double() - ref).abs().max() / ref.abs().max())
-    return {"forms": res}
+        del o
+    res["DS_max_rel_err_vs_P64"] = max(float((x.double() - y.double()).abs().max() / y.double().abs().max())
+                                       for x, y in zip(h.outs, ref))
+    return res
 
 
 if __name__ == "__main__":

@@ -228,14 +228,18 @@ void krig_plan_destroy(krig_plan_t plan);
  *
  * The first call on a device looks up the array's device address (a one-time
  * set-up per device, done with that device current); make that first call
- * before any stream capture.
+ * before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device, do not call this entry point on
+ * that device again.
  *
  * Arguments: as one volume of krig_interpolate (desc, d_slices, d_out,
- * d_var nullable, d_params pointing at one device krig_variogram).  With
+ * d_var nullable, d_params pointing at one device krig_variogram); the
+ * descriptor limits and error codes are those of krig_plan_create.  With
  * check_status != 0 the call waits for the stream and returns KRIG_ESINGULAR
- * if a kriging system was singular; with 0 it returns after enqueueing (a
- * singular system then shows as NaN estimates).  No cudaMalloc, cudaFree or
- * other allocating call is made. */
+ * if a kriging system was singular, or KRIG_ETIMEOUT if a bounded device
+ * wait gave up (part of the output is then not written); with 0 it returns
+ * after enqueueing (a singular system then shows as NaN estimates).  No
+ * cudaMalloc, cudaFree or other allocating call is made. */
 krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d_slices, void* d_out, float* d_var,
                                      const krig_variogram* d_params, int32_t check_status, void* stream);
 

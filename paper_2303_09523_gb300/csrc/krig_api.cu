@@ -67,7 +67,9 @@ struct krig_plan_s {
     int64_t launches[KRIG_TIMING_KINDS] = {0, 0, 0, 0};
 };
 
-static krig_status check_desc(const krig_volume_desc& d, int i)
+// Descriptor limits of include/krig.h, shared by krig_plan_create and
+// krig_interpolate_noalloc (declared in krig_internal.h).
+krig_status krig_internal_check_desc(const krig_volume_desc& d, int i)
 {
     if (d.H < 1 || d.H > 65536 || d.W < 1 || d.W > 65536)
         return fail(KRIG_EINVAL, "volume %d: H, W must be in [1, 65536] (got %d x %d)", i, d.H, d.W);
@@ -133,7 +135,7 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
     const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT | KRIG_FLAG_LOO;
     if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
     for (int i = 0; i < n_vols; ++i) {
-        krig_status st = check_desc(vols[i], i);
+        krig_status st = krig_internal_check_desc(vols[i], i);
         if (st != KRIG_OK) return st;
         if ((flags & KRIG_FLAG_LOO) && vols[i].n_known < 3)
             return fail(KRIG_EINVAL, "volume %d: leave-one-slice-out needs n_known >= 3", i);

@@ -127,6 +127,9 @@ int krig_device_sm_count();
 
 // Set the thread-local message returned by krig_last_error() (krig_api.cu).
 __attribute__((visibility("hidden"))) void krig_internal_set_error(const char* msg);
+// Check one volume descriptor against the limits of include/krig.h (volume
+// index i for the message); sets the message and returns the status.
+__attribute__((visibility("hidden"))) krig_status krig_internal_check_desc(const krig_volume_desc& d, int i);
 
 // Table sizes (bytes) per volume for the DS form.
 inline int64_t krig_wtab_bytes(const KrigVol& v)

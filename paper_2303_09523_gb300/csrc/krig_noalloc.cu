@@ -13,7 +13,10 @@
 // that every GPU loading the library keeps until the process exits.  Host code
 // cannot pass that array's name to a kernel (on the host it only names a
 // host-side stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress and cached.  The cache outlives the device's primary
+// context: after cudaDeviceReset the module is loaded again at another
+// address, so this entry point must not be called on that device again in
+// the same process.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -68,12 +71,8 @@ extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, co
     if (!desc || !d_slices || !d_out || !d_params)
         return noalloc_fail(KRIG_EINVAL, "desc, d_slices, d_out and d_params must not be NULL");
     const krig_volume_desc& d = *desc;
-    if (d.H < 1 || d.H > 65536 || d.W < 1 || d.W > 65536 || d.n_known < 2 || d.n_known > 65536 ||
-        d.zfactor < 1 || d.zfactor > KRIG_GMAX || d.n_sub_blocks < 1 || d.n_sub_blocks > d.n_known - 1 ||
-        d.half_w < 0 || d.half_w > KRIG_RMAX ||
-        (d.in_dtype != KRIG_F64 && d.in_dtype != KRIG_F32 && d.in_dtype != KRIG_U16) ||
-        (d.in_dtype == KRIG_U16 && !(d.in_scale > 0.0f && d.in_scale < 3.0e38f)))
-        return noalloc_fail(KRIG_EINVAL, "invalid volume descriptor (same limits as krig_plan_create)");
+    krig_status chk = krig_internal_check_desc(d, 0);  // the same limits as krig_plan_create
+    if (chk != KRIG_OK) return chk;
     if ((uintptr_t)d_slices % 16 || (uintptr_t)d_out % 16 || (d_var && (uintptr_t)d_var % 16))
         return noalloc_fail(KRIG_EINVAL, "slice, output and variance buffers must be 16-byte aligned");
 
@@ -122,6 +121,8 @@ extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, co
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return noalloc_fail(KRIG_ECUDA, std::string("reading the status word: ") + cudaGetErrorString(e));
         if (bits & KRIG_DEV_SINGULAR) return noalloc_fail(KRIG_ESINGULAR, "a kriging system was singular");
+        // a stencil wait that gave up left part of the output unwritten
+        if (bits & KRIG_DEV_TIMEOUT) return noalloc_fail(KRIG_ETIMEOUT, "a device-side wait timed out");
     }
     return KRIG_OK;
 }

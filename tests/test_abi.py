@@ -137,3 +137,27 @@ def test_empirical_variogram_rejects_before_any_launch(lib, bad, lag):
                                         None) == binding.KRIG_EINVAL
     assert lib.krig_empirical_variogram(ctypes.byref(vd), None, 2, ctypes.c_void_p(256), None,
                                         None) == binding.KRIG_EINVAL
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(H=0), binding.KRIG_EINVAL),
+    (dict(n_known=1), binding.KRIG_EINVAL),
+    (dict(zfactor=9), binding.KRIG_EINVAL),
+    (dict(n_sub_blocks=9), binding.KRIG_EINVAL),
+    (dict(half_w=3), binding.KRIG_EUNSUPPORTED),
+    (dict(in_dtype=7), binding.KRIG_EINVAL),
+    (dict(in_dtype=binding.U16, in_scale=0.0), binding.KRIG_EINVAL),
+])
+def test_noalloc_rejects_what_plan_create_rejects(lib, bad, status):
+    """The allocation-free entry point checks a descriptor with the planner's own check,
+    before any CUDA call, and returns the same status."""
+    d = _desc(**bad)
+    vd = binding.VolumeDesc(d["H"], d["W"], d["n_known"], d["zfactor"], d["n_sub_blocks"], d["half_w"],
+                            d["in_dtype"], d["in_scale"])
+    fn = lib.krig_interpolate_noalloc
+    fn.argtypes = [ctypes.POINTER(binding.VolumeDesc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    st = fn(ctypes.byref(vd), 256, 256, None, 256, 1, None)
+    assert st == status == _create([d])[0]
+    assert len(lib.krig_last_error()) > 0

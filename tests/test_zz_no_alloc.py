@@ -72,3 +72,23 @@ def test_noalloc_rejects_volume_beyond_static_scratch():
     st, _, _ = _run_noalloc(fn, vol, t, params)
     assert st == binding.KRIG_EINVAL
     assert b"scratch" in binding.lib().krig_last_error()
+
+
+def test_noalloc_reports_singular_then_recovers():
+    """A singular variogram (nugget = sill = 0) is reported as KRIG_ESINGULAR; the next call
+    in the same shared scratch starts from a cleared status word, returns KRIG_OK and matches
+    the workspace entry point."""
+    fn = _noalloc_fn()
+    vol = phantoms.random_stack(5, 40, 52, 3, 1, k=2, seed=33)
+    t = torch.from_numpy(np.ascontiguousarray(vol.slices)).cuda()
+    bad = binding.variogram_tensor([dict(model="spherical", nugget=0.0, sill=0.0, range=8.0)], device=t.device)
+    st, _, _ = _run_noalloc(fn, vol, t, bad)
+    assert st == binding.KRIG_ESINGULAR
+    assert b"singular" in binding.lib().krig_last_error()
+    good = binding.variogram_tensor([vol.variogram()], device=t.device)
+    st, out, var = _run_noalloc(fn, vol, t, good)
+    assert st == binding.KRIG_OK, binding.lib().krig_last_error()
+    ref, rvar = _reference(vol, t)
+    err = float((out.double() - ref.double()).abs().max() / ref.double().abs().max())
+    assert err <= TOL
+    assert torch.equal(out[::vol.zfactor], ref[::vol.zfactor])
