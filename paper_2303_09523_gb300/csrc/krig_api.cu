@@ -169,6 +169,7 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
     L.n_items = items;
     L.n_classes = classes;
     L.n_vox = vox;
+    krig_ds_order(L);
     p->ws_bytes = off;
     if (workspace_bytes_out) *workspace_bytes_out = (size_t)off;
     *plan = p;
@@ -301,17 +302,14 @@ krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const k
 static void set_chunk(krig_plan_t plan, int chunk)
 {
     KrigLaunch& L = plan->L;
-    int64_t items = 0;
     for (int v = 0; v < L.n_vols; ++v) {
         KrigVol& V = L.vol[v];
         const int max_block = (V.n - 1 + V.k - 1) / V.k;
         V.chunk = chunk < 1 ? 1 : (chunk > max_block ? max_block : chunk);
         V.chunks = (max_block + V.chunk - 1) / V.chunk;
         V.mdiv_chunks = krig_udiv_magic((uint32_t)V.chunks);
-        V.item_begin = items;
-        items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
     }
-    L.n_items = items;
+    krig_ds_order(L);
 }
 
 krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, void* const* d_out,

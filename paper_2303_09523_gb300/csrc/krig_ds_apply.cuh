@@ -6,18 +6,23 @@
 // work items of Algorithm 1: an item is one 64 x 16 in-plane tile of a run of
 // consecutive gaps ("chunk") inside one Z sub-block.  The item's known slices
 // (tile plus halo) stream through a ring of shared-memory slots filled by the
-// TMA bulk-copy engine (cp.async.bulk, completion on an mbarrier), one slice
-// ahead of the compute, so each known slice of the chunk is read from memory
-// once.  The item writes its output slices -- the bit-exact copy of its known
-// slices (Algorithm 1 step 3) and the interpolated ones -- straight to their
-// final offsets (the merge of Sec. 4.2).
+// TMA engine (completion on an mbarrier), ahead of the compute, so each known
+// slice of the chunk is read from memory once.  The item writes its output
+// slices -- the bit-exact copy of its known slices (Algorithm 1 step 3) and the
+// interpolated ones -- straight to their final offsets (the merge of Sec. 4.2).
 //
 // Interior pixels (full window) use the D4 symmetry of the interior class:
 // the taps of each orbit {same max(|dx|,|dy|), min(|dx|,|dy|)} share one
 // weight, so the stencil is applied to orbit sums (6 per slice for r = 2)
-// instead of 25 taps.  Pixels within r of the slice border take the general
-// path with the full weight row of their own class.  A warp covers a 16 x 8
-// block of pixels (four per thread), so only warps at the border diverge.
+// instead of 25 taps; a slice's orbit sums serve both gaps it brackets.
+// Pixels within r of the slice border ("frame" pixels) take the general path
+// with the full weight row of their own class, in units of 32 handed out by a
+// ticket counter to the frame warp and, after their items, the consumer warps.
+//
+// Items are numbered by input type and stencil shape (the host sorts the
+// volumes), so each block walks one contiguous range per shape, round-robin
+// across blocks, and every per-item lookup reads a per-block copy of the
+// volume table in shared memory.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -237,9 +242,146 @@ __device__ __forceinline__ void ds_plain_fill(TI* slot, uint64_t* bar, const TI*
 }
 
 // ---------------------------------------------------------------------------
-// Accumulation
+// Per-volume record of the stencil, copied once per block into shared memory
+// (the kernel parameter block holds every field, but reads that miss the
+// constant cache cost a round trip each; the item and frame loops read these).
 // ---------------------------------------------------------------------------
+struct DsVolS {
+    const void* in;
+    void* out;
+    float* var;
+    uint64_t mt, mc, mx;           // multiply-high divisors: tiles, chunks, tiles_x
+    int64_t wtab_off, vtab_off, otab_off;
+    int32_t item_begin, item_end;  // work items [begin, end)
+    int32_t frame_begin, frame_end;  // frame units [begin, end) among the volumes of this input type
+    int32_t H, W, n, g;
+    int32_t r, dtype, tiles_x, tiles;
+    int32_t chunks, chunk, gq, grm;
+    int32_t cint, n_frame, frame_units, ncx;
+    float scale;
+    int8_t xmap[(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
+    int8_t ymap[(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
+    int8_t pad[2];
+};
+static_assert(sizeof(DsVolS) % 16 == 0, "DsVolS must keep 16-byte alignment of the table");
 
+__device__ __forceinline__ void ds_fill_vols(const KrigLaunch& P, DsVolS* tab)
+{
+    for (int v = threadIdx.x; v < P.n_vols; v += blockDim.x) {
+        const KrigVol& V = P.vol[v];
+        DsVolS s;
+        s.in = P.in[v];
+        s.out = P.out[v];
+        s.var = P.var[v];
+        s.mt = V.mdiv_tiles;
+        s.mc = V.mdiv_chunks;
+        s.mx = V.mdiv_tx;
+        s.wtab_off = V.wtab_off;
+        s.vtab_off = V.vtab_off;
+        s.otab_off = V.otab_off;
+        s.item_begin = (int32_t)V.item_begin;
+        s.item_end = (int32_t)(V.item_begin + (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y);
+        s.frame_begin = (int32_t)V.frame_begin;
+        s.frame_end = (int32_t)(V.frame_begin + (int64_t)(V.n - 1) * V.frame_units);
+        s.H = V.H;
+        s.W = V.W;
+        s.n = V.n;
+        s.g = V.g;
+        s.r = V.r;
+        s.dtype = V.dtype;
+        s.tiles_x = V.tiles_x;
+        s.tiles = V.tiles_x * V.tiles_y;
+        s.chunks = V.chunks;
+        s.chunk = V.chunk;
+        s.gq = V.gq;
+        s.grm = V.grm;
+        s.cint = V.cint;
+        s.n_frame = V.n_frame;
+        s.frame_units = V.frame_units;
+        s.ncx = V.ncx;
+        s.scale = V.scale;
+        for (int i = 0; i < (KRIG_RMAX + 1) * (KRIG_RMAX + 1); ++i) {
+            s.xmap[i] = V.xmap[i];
+            s.ymap[i] = V.ymap[i];
+        }
+        s.pad[0] = s.pad[1] = 0;
+        tab[v] = s;
+    }
+}
+
+// Dynamic shared memory of k_ds_apply: DS_STAGES ring slots, the full and
+// empty barriers, the test barrier, the abort flag and the per-warp "weights
+// not yet waited for" flags, the interior orbit weights of every volume and
+// the volume table.  Offsets depend on the number of volumes.
+extern __shared__ __align__(128) unsigned char ds_smem[];
+template <typename TI> struct DsLayout {
+    typedef typename DsTypes<TI>::TC TC;
+    static constexpr int S = DsStages<TI>::S;
+    static constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;  // slot stride, elements
+    static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
+    static constexpr size_t flag_off = bar_off + (2 * S + 1) * sizeof(uint64_t);
+    static constexpr size_t ow_off = (flag_off + 4 * (1 + DS_CONSUMERS) + 15) / 16 * 16;
+    static constexpr size_t ow_per_vol = 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(TC);
+    __host__ __device__ static constexpr size_t vol_off(int nv) { return ow_off + (size_t)nv * ow_per_vol; }
+    __host__ __device__ static constexpr size_t bytes(int nv) { return vol_off(nv) + (size_t)nv * sizeof(DsVolS); }
+    __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
+    __device__ static __forceinline__ uint64_t* full() { return (uint64_t*)(ds_smem + bar_off); }
+    __device__ static __forceinline__ uint64_t* empty() { return (uint64_t*)(ds_smem + bar_off) + S; }
+    __device__ static __forceinline__ uint64_t* never() { return (uint64_t*)(ds_smem + bar_off) + 2 * S; }
+    __device__ static __forceinline__ int* abort_flag() { return (int*)(ds_smem + flag_off); }
+    __device__ static __forceinline__ int* pending(int warp) { return (int*)(ds_smem + flag_off) + 1 + warp; }
+    __device__ static __forceinline__ TC* ow() { return (TC*)(ds_smem + ow_off); }
+    __device__ static __forceinline__ const DsVolS* vols(int nv) { return (const DsVolS*)(ds_smem + vol_off(nv)); }
+};
+
+struct DsItem {
+    int c0, c1, x0, y0;
+};
+
+// item -> (sub-block b, chunk ch, tile): item = (b * chunks + ch) * tiles + tile,
+// divisions by multiply-high.
+__device__ __forceinline__ bool ds_decode(const DsVolS& V, int it, DsItem& d)
+{
+    const uint32_t local = (uint32_t)(it - V.item_begin);
+    const uint32_t rest = krig_udiv(local, V.mt), tile = local - rest * (uint32_t)V.tiles;
+    const uint32_t bb = krig_udiv(rest, V.mc), ch = rest - bb * (uint32_t)V.chunks;
+    const uint32_t ty = krig_udiv(tile, V.mx), tx = tile - ty * (uint32_t)V.tiles_x;
+    const int b = (int)bb;
+    const int a0 = b * V.gq + min(b, V.grm), a1 = (b + 1) * V.gq + min(b + 1, V.grm);
+    d.c0 = a0 + (int)ch * V.chunk;
+    d.c1 = min(d.c0 + V.chunk, a1);
+    d.x0 = (int)tx * KRIG_TX;
+    d.y0 = (int)ty * KRIG_TY;
+    return d.c0 < d.c1;
+}
+
+// Stencil shape of a volume: (r, g).
+__device__ __forceinline__ int ds_shape(const DsVolS& V) { return V.r * 8 + V.g - 1; }
+
+// The run of volumes [k, *k_end) in item order that share the input type and
+// shape of ds_order[k]; false if ds_order[k] is of another input type.
+__device__ __forceinline__ bool ds_run(const int8_t* order, const DsVolS* tab, int nv, int dtype, int k, int* k_end)
+{
+    const DsVolS& V = tab[order[k]];
+    int e = k + 1;
+    while (e < nv && tab[order[e]].dtype == V.dtype && ds_shape(tab[order[e]]) == ds_shape(V)) ++e;
+    *k_end = e;
+    return V.dtype == dtype;
+}
+
+// First item >= lo of this block's round-robin sequence it = blockIdx.x (mod grid).
+__device__ __forceinline__ int ds_first_item(int lo)
+{
+    const int G = (int)gridDim.x, b = (int)blockIdx.x;
+    return lo + (((b - lo) % G) + G) % G;
+}
+
+// ---------------------------------------------------------------------------
+// Interior path: D4 orbit sums of one known slice around the thread's four
+// pixels (orbits {same max(|dx|,|dy|), min(|dx|,|dy|)}: 1, 3, 6 for r = 0, 1, 2),
+// computed once per slice and kept in registers for both gaps the slice
+// brackets; then one weight per orbit and target.
+// ---------------------------------------------------------------------------
 // Two floats as one 64-bit register pair and back (operands of the packed
 // f32x2 instructions).
 __device__ __forceinline__ unsigned long long pk2(float a, float b)
@@ -252,262 +394,146 @@ __device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
 }
+
+template <int R> struct DsNO { static constexpr int N = R == 0 ? 1 : (R == 1 ? 3 : 6); };
 template <int GM1> struct DsGP { static constexpr int N = GM1 > 0 ? GM1 : 1; };  // accumulators per pixel
 
-// Interior path: orbit sums of each slice times the interior orbit weights.
-// ow: shared [2][KRIG_NORB][8] orbit weights.
-template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_accum_interior(typename DsTypes<TI>::TC (&acc)[KRIG_PX][DsGP<GM1>::N],
-                                                  const TI* lo, const TI* hi, int lrow, int lcol,
-                                                  const typename DsTypes<TI>::TC* ow)
+template <typename TI, int R>
+__device__ __forceinline__ void ds_orbits(const TI* slot, int lrow, int lcol,
+                                          typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
 {
     typedef typename DsTypes<TI>::TC TC;
     constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    constexpr int NO = R == 0 ? 1 : (R == 1 ? 3 : 6);
+    // columns 4-R .. 7+R of the 12 loaded around the thread's four pixels
+    TC c0[12], a1[12], a2[12];
+    {
+        const TI* rowp = slot + (lrow + R) * RP + PAD + lcol;
+        TC a[4], b[4], c[4];
+        if (R > 0) ld4(rowp - 4, a);
+        ld4(rowp, b);
+        if (R > 0) ld4(rowp + 4, c);
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const TI* slot = s == 0 ? lo : hi;
-        // columns 4-R .. 7+R of the 12 loaded around the thread's four pixels
-        TC c0[12], a1[12], a2[12];
-        {
-            const TI* rowp = slot + (lrow + R) * RP + PAD + lcol;
-            TC a[4], b[4], c[4];
-            ld4(rowp - 4, a);
-            ld4(rowp, b);
-            ld4(rowp + 4, c);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                c0[q] = a[q];
-                c0[4 + q] = b[q];
-                c0[8 + q] = c[q];
-            }
+        for (int q = 0; q < 4; ++q) {
+            c0[q] = R > 0 ? a[q] : TC(0);
+            c0[4 + q] = b[q];
+            c0[8 + q] = R > 0 ? c[q] : TC(0);
         }
-        if (R >= 1) {
-            const TI* rm = slot + (lrow + R - 1) * RP + PAD + lcol;
-            const TI* rp = slot + (lrow + R + 1) * RP + PAD + lcol;
-            TC a[4], b[4], c[4], d[4], e[4], f[4];
-            ld4(rm - 4, a);
-            ld4(rm, b);
-            ld4(rm + 4, c);
-            ld4(rp - 4, d);
-            ld4(rp, e);
-            ld4(rp + 4, f);
+    }
+    if (R >= 1) {
+        const TI* rm = slot + (lrow + R - 1) * RP + PAD + lcol;
+        const TI* rp = slot + (lrow + R + 1) * RP + PAD + lcol;
+        TC a[4], b[4], c[4], d[4], e[4], f[4];
+        ld4(rm - 4, a);
+        ld4(rm, b);
+        ld4(rm + 4, c);
+        ld4(rp - 4, d);
+        ld4(rp, e);
+        ld4(rp + 4, f);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a1[q] = a[q] + d[q];
-                a1[4 + q] = b[q] + e[q];
-                a1[8 + q] = c[q] + f[q];
-            }
+        for (int q = 0; q < 4; ++q) {
+            a1[q] = a[q] + d[q];
+            a1[4 + q] = b[q] + e[q];
+            a1[8 + q] = c[q] + f[q];
+        }
+    }
+    if (R >= 2) {
+        const TI* rm = slot + (lrow + R - 2) * RP + PAD + lcol;
+        const TI* rp = slot + (lrow + R + 2) * RP + PAD + lcol;
+        TC a[4], b[4], c[4], d[4], e[4], f[4];
+        ld4(rm - 4, a);
+        ld4(rm, b);
+        ld4(rm + 4, c);
+        ld4(rp - 4, d);
+        ld4(rp, e);
+        ld4(rp + 4, f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a2[q] = a[q] + d[q];
+            a2[4 + q] = b[q] + e[q];
+            a2[8 + q] = c[q] + f[q];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < KRIG_PX; ++p) {
+        const int m = 4 + p;  // centre column
+        orb[p][0] = c0[m];
+        if (R >= 1) {
+            orb[p][1] = (c0[m - 1] + c0[m + 1]) + a1[m];
+            orb[p][2] = a1[m - 1] + a1[m + 1];
         }
         if (R >= 2) {
-            const TI* rm = slot + (lrow + R - 2) * RP + PAD + lcol;
-            const TI* rp = slot + (lrow + R + 2) * RP + PAD + lcol;
-            TC a[4], b[4], c[4], d[4], e[4], f[4];
-            ld4(rm - 4, a);
-            ld4(rm, b);
-            ld4(rm + 4, c);
-            ld4(rp - 4, d);
-            ld4(rp, e);
-            ld4(rp + 4, f);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a2[q] = a[q] + d[q];
-                a2[4 + q] = b[q] + e[q];
-                a2[8 + q] = c[q] + f[q];
-            }
+            orb[p][3] = (c0[m - 2] + c0[m + 2]) + a2[m];
+            orb[p][4] = (a1[m - 2] + a1[m + 2]) + (a2[m - 1] + a2[m + 1]);
+            orb[p][5] = a2[m - 2] + a2[m + 2];
         }
-        TC orb[KRIG_PX][NO];
+    }
+}
+
+// The thread's four pixel values of one known slice (the orbit-0 sums).
+template <typename TI, int R>
+__device__ __forceinline__ void ds_centres(const TI* slot, int lrow, int lcol,
+                                           typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
+{
+    typedef typename DsTypes<TI>::TC TC;
+    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
+    TC b[4];
+    ld4(slot + (lrow + R) * RP + PAD + lcol, b);
 #pragma unroll
-        for (int p = 0; p < KRIG_PX; ++p) {
-            const int m = 4 + p;  // centre column
-            orb[p][0] = c0[m];
-            if (R >= 1) {
-                orb[p][1] = (c0[m - 1] + c0[m + 1]) + a1[m];
-                orb[p][2] = a1[m - 1] + a1[m + 1];
-            }
-            if (R >= 2) {
-                orb[p][3] = (c0[m - 2] + c0[m + 2]) + a2[m];
-                orb[p][4] = (a1[m - 2] + a1[m + 2]) + (a2[m - 1] + a2[m + 1]);
-                orb[p][5] = a2[m - 2] + a2[m + 2];
-            }
-        }
+    for (int p = 0; p < KRIG_PX; ++p) {
+        orb[p][0] = b[p];
 #pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            TC w[8];
-            ldw8(ow + (s * KRIG_NORB + o) * KRIG_TSLOTS, w);
+        for (int o = 1; o < DsNO<R>::N; ++o) orb[p][o] = TC(0);
+    }
+}
+
+// Targets t0 and t0 + 1 (t0 + 1 < GM1 or not) of the four pixels from the orbit
+// sums of both slices: acc[p][i] = sum_o wl[o][t0+i] lo[p][o] + wh[o][t0+i] hi[p][o];
+// ow: the item's [2][NORB][8] orbit weights in shared memory.  One target pair
+// at a time keeps few accumulators live beside the two slices' orbit sums.
+template <typename TI, int R, int GM1>
+__device__ __forceinline__ void ds_fma_pair(typename DsTypes<TI>::TC (&acc)[KRIG_PX][2], int t0,
+                                            const typename DsTypes<TI>::TC (&lo)[KRIG_PX][DsNO<R>::N],
+                                            const typename DsTypes<TI>::TC (&hi)[KRIG_PX][DsNO<R>::N],
+                                            const typename DsTypes<TI>::TC* ow)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    const bool two = t0 + 1 < GM1;
+#pragma unroll
+    for (int p = 0; p < KRIG_PX; ++p) acc[p][0] = acc[p][1] = TC(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int o = 0; o < DsNO<R>::N; ++o) {
+            const TC* wp = ow + (s * KRIG_NORB + o) * KRIG_TSLOTS + t0;
             if constexpr (sizeof(TC) == 4) {
                 // two targets per packed FMA (fma.rn.f32x2: each half rounds as fmaf)
+                const float2 w = *(const float2*)wp;
+                const unsigned long long wpk = pk2(w.x, w.y);
 #pragma unroll
                 for (int p = 0; p < KRIG_PX; ++p) {
-                    const unsigned long long ob = pk2(orb[p][o], orb[p][o]);
-#pragma unroll
-                    for (int t = 0; t + 1 < GM1; t += 2) {
-                        unsigned long long a2 = pk2(acc[p][t], acc[p][t + 1]);
-                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(pk2(w[t], w[t + 1])), "l"(ob));
-                        upk2(a2, acc[p][t], acc[p][t + 1]);
+                    const TC z = s == 0 ? lo[p][o] : hi[p][o];
+                    if (two) {
+                        unsigned long long a2 = pk2(acc[p][0], acc[p][1]);
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(wpk), "l"(pk2(z, z)));
+                        upk2(a2, acc[p][0], acc[p][1]);
+                    } else {
+                        acc[p][0] = fmaf(w.x, z, acc[p][0]);
                     }
-                    if (GM1 & 1) acc[p][GM1 - 1] = fmaf(w[GM1 - 1], orb[p][o], acc[p][GM1 - 1]);
                 }
             } else {
+                const double2 w = *(const double2*)wp;
 #pragma unroll
-                for (int p = 0; p < KRIG_PX; ++p)
-#pragma unroll
-                    for (int t = 0; t < GM1; ++t) acc[p][t] = fma(w[t], orb[p][o], acc[p][t]);
+                for (int p = 0; p < KRIG_PX; ++p) {
+                    const TC z = s == 0 ? lo[p][o] : hi[p][o];
+                    acc[p][0] = fma(w.x, z, acc[p][0]);
+                    if (two) acc[p][1] = fma(w.y, z, acc[p][1]);
+                }
             }
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// Persistent producer / consumer pipeline
-//
-// Blocks walk the work items round-robin, shape by shape.  Warp DS_PRODUCER
-// streams every known slice the block needs, item after item, into a ring of
-// DS_STAGES slots ("full" barrier per slot, completed by the bulk copy), after
-// the consumers released the slot's previous slice ("empty" barrier, one
-// arrival per consumer warp).  The consumer warps compute gap after gap; they
-// never wait on each other.  Warp DS_FRAMER computes the border pixels beside
-// them.  Every wait is bounded; a wait that gives up sets the device status
-// KRIG_DEV_TIMEOUT and the shared abort flag, and the producer then waits
-// (bounded) for the copies it still has in flight.
-// ---------------------------------------------------------------------------
-struct DsItem {
-    int v, x0, y0, c0, c1;
-};
-
-// Stencil shape of a volume: (r, g) as r * 8 + g - 1.  A block takes its
-// items shape by shape (ascending), round-robin within a shape, so that each
-// shape's loop runs in code compiled for that shape alone.
-#define DS_NSHAPE ((KRIG_RMAX + 1) * 8)
-__device__ __forceinline__ int ds_shape(const KrigVol& V) { return V.r * 8 + V.g - 1; }
-
-__device__ __forceinline__ uint32_t ds_shape_mask(const KrigLaunch& P, int dtype)
-{
-    uint32_t m = 0;
-    for (int v = 0; v < P.n_vols; ++v)
-        if (P.vol[v].dtype == dtype) m |= 1u << ds_shape(P.vol[v]);
-    return m;
-}
-
-__device__ __forceinline__ bool ds_decode(const KrigLaunch& P, int it, int dtype, int shape, DsItem& d)
-{
-    int v = 0;
-    for (int u = 1; u < P.n_vols; ++u)
-        if (P.vol[u].item_begin <= it) v = u;
-    const KrigVol& V = P.vol[v];
-    if (V.dtype != dtype || ds_shape(V) != shape) return false;
-    // item = ((sub-block b) * chunks + chunk ch) * tiles + tile, divisions by multiply-high
-    const uint32_t local = (uint32_t)(it - (int)V.item_begin);
-    const uint32_t rest = krig_udiv(local, V.mdiv_tiles), tile = local - rest * (uint32_t)(V.tiles_x * V.tiles_y);
-    const uint32_t bb = krig_udiv(rest, V.mdiv_chunks), ch = rest - bb * (uint32_t)V.chunks;
-    const uint32_t ty = krig_udiv(tile, V.mdiv_tx), tx = tile - ty * (uint32_t)V.tiles_x;
-    const int b = (int)bb;
-    const int a0 = b * V.gq + min(b, V.grm), a1 = (b + 1) * V.gq + min(b + 1, V.grm);
-    d.v = v;
-    d.c0 = a0 + (int)ch * V.chunk;
-    d.c1 = min(d.c0 + V.chunk, a1);
-    d.x0 = (int)tx * KRIG_TX;
-    d.y0 = (int)ty * KRIG_TY;
-    return d.c0 < d.c1;
-}
-
-// The fields of one volume that the consumer loop needs, one copy per warp in
-// shared memory: read from the kernel parameters once per volume instead of
-// once per item (parameter reads that miss the constant cache take a round
-// trip to L2), without holding registers across the loop.
-template <typename TI>
-struct DsVolR {
-    int v, match;                 // volume index; its items are of this kernel's type and shape
-    int item_begin, tiles_x, tiles, chunks, chunk, gq, grm;
-    uint64_t mt, mc, mx;          // multiply-high divisors: tiles, chunks, tiles_x
-    int H, W, g, jlast, cint;
-    float scale;
-    typename DsTypes<TI>::TO* out;
-    float* var;
-    const float* vt;
-};
-
-template <typename TI>
-__device__ __forceinline__ DsVolR<TI> ds_volr(const KrigLaunch& P, int v, int dtype, int shape)
-{
-    typedef typename DsTypes<TI>::TO TO;
-    const KrigVol& V = P.vol[v];
-    DsVolR<TI> R;
-    R.v = v;
-    R.match = V.dtype == dtype && ds_shape(V) == shape;
-    R.item_begin = (int)V.item_begin;
-    R.tiles_x = V.tiles_x;
-    R.tiles = V.tiles_x * V.tiles_y;
-    R.chunks = V.chunks;
-    R.chunk = V.chunk;
-    R.gq = V.gq;
-    R.grm = V.grm;
-    R.mt = V.mdiv_tiles;
-    R.mc = V.mdiv_chunks;
-    R.mx = V.mdiv_tx;
-    R.H = V.H;
-    R.W = V.W;
-    R.g = V.g;
-    R.jlast = V.n - 2;
-    R.cint = V.cint;
-    R.scale = V.scale;
-    R.out = (TO*)P.out[v];
-    R.var = P.var[v];
-    R.vt = (const float*)(P.ws + V.vtab_off) + (int64_t)max(V.cint, 0) * KRIG_TSLOTS;
-    return R;
-}
-
-// ds_decode on the register copy.
-template <typename TI>
-__device__ __forceinline__ bool ds_decode_r(const DsVolR<TI>& R, int it, DsItem& d)
-{
-    const uint32_t local = (uint32_t)(it - R.item_begin);
-    const uint32_t rest = krig_udiv(local, R.mt), tile = local - rest * (uint32_t)R.tiles;
-    const uint32_t bb = krig_udiv(rest, R.mc), ch = rest - bb * (uint32_t)R.chunks;
-    const uint32_t ty = krig_udiv(tile, R.mx), tx = tile - ty * (uint32_t)R.tiles_x;
-    const int b = (int)bb;
-    const int a0 = b * R.gq + min(b, R.grm), a1 = (b + 1) * R.gq + min(b + 1, R.grm);
-    d.v = R.v;
-    d.c0 = a0 + (int)ch * R.chunk;
-    d.c1 = min(d.c0 + R.chunk, a1);
-    d.x0 = (int)tx * KRIG_TX;
-    d.y0 = (int)ty * KRIG_TY;
-    return d.c0 < d.c1;
-}
-
-struct DsShared {
-    void* ow;          // interior orbit weights of every volume, [v][2][NORB][8]
-    uint64_t* full;
-    uint64_t* empty;
-    uint64_t* never;  // test hook: a barrier nothing completes
-    int* abort;
-};
-
-// Dynamic shared memory of k_ds_apply: DS_STAGES slots, the full and empty
-// barriers, the test barrier, the abort flag, the orbit weights.  Functions
-// derive the pointers from the base themselves (nothing goes through the
-// stack of a non-inlined call).
-extern __shared__ __align__(128) unsigned char ds_smem[];
-template <typename TI> struct DsLayout {
-    static constexpr int S = DsStages<TI>::S;
-    static constexpr int stride = (KRIG_TY + 2 * KRIG_RMAX) * DsTypes<TI>::RP;  // slot stride, elements
-    static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
-    static constexpr size_t ow_bytes =
-        (size_t)KRIG_MAX_VOLUMES * 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(typename DsTypes<TI>::TC);
-    static constexpr size_t vr_off = (bar_off + (2 * S + 2) * sizeof(uint64_t) + ow_bytes + 15) / 16 * 16;
-    static constexpr size_t bytes = vr_off + DS_CONSUMERS * sizeof(DsVolR<TI>);
-    __device__ static __forceinline__ DsVolR<TI>* volr(int warp) { return (DsVolR<TI>*)(ds_smem + vr_off) + warp; }
-    __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
-    __device__ static __forceinline__ DsShared shared()
-    {
-        uint64_t* bars = (uint64_t*)(ds_smem + bar_off);
-        return DsShared{(void*)(bars + 2 * S + 2), bars, bars + S, bars + 2 * S, (int*)(bars + 2 * S + 1)};
-    }
-};
-
-// Per-item constants of a consumer thread, taken out of the kernel parameters
-// once per item: inside the slice loop the barrier waits (asm with a memory
-// clobber) would otherwise force every parameter read to be repeated.
+// Per-item constants of a consumer thread.
 template <typename TI>
 struct DsCtx {
     typename DsTypes<TI>::TO* out;  // output at this thread's first pixel, slice 0
@@ -521,22 +547,24 @@ struct DsCtx {
 };
 
 template <typename TI, int R>
-__device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolR<TI>& V, const DsItem& d, int lrow, int lcol, bool dry)
+__device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolS& V, const unsigned char* ws, const DsItem& d, int lrow,
+                                            int lcol, bool dry)
 {
+    typedef typename DsTypes<TI>::TO TO;
     DsCtx<TI> c;
     const int H = V.H, W = V.W;
     const int y = d.y0 + lrow, xb = d.x0 + lcol;
     c.plane = (int64_t)H * W;
     c.g = V.g;
-    c.jlast = V.jlast;
+    c.jlast = V.n - 2;
     c.scale = V.scale;
     c.nvalid = min(KRIG_PX, W - xb);
     c.mine = y < H && c.nvalid > 0;
     c.vec_out = (W % KRIG_PX == 0) && c.nvalid == KRIG_PX;
     const int64_t pix = c.mine ? (int64_t)y * W + xb : 0;
-    c.out = V.out + pix;
+    c.out = (TO*)V.out + pix;
     c.var = (dry || !V.var) ? nullptr : V.var + pix;
-    c.vt = V.vt;
+    c.vt = (const float*)(ws + V.vtab_off) + (int64_t)max(V.cint, 0) * KRIG_TSLOTS;
     // interior pixels of the four: rows y in [R, H-1-R], x in [R, W-1-R]
     c.plo = max(0, R - xb);
     c.phi = min(c.nvalid, W - R - xb);
@@ -545,87 +573,200 @@ __device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolR<TI>& V, const DsItem& d
     return c;
 }
 
-// One gap of one item for the consumer warps: passthrough of known slice j
-// for every pixel, and the g-1 interpolated slices (with variance) for the
-// interior pixels, through the orbit sums.  Frame pixels (within r of the
-// border) are written by the frame warp instead.
-template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_gap(const DsCtx<TI>& c, int j, const TI* lo, const TI* hi, int lrow, int lcol,
-                                       const typename DsTypes<TI>::TC* ow, bool dry)
+// Known slice -> its output slice, bit-exact (u16: float32(u) * scale).
+template <typename TI, int R>
+__device__ __forceinline__ void ds_passthrough(const DsCtx<TI>& c, int64_t off,
+                                               const typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
 {
-    typedef typename DsTypes<TI>::TC TC;
     typedef typename DsTypes<TI>::TO TO;
-    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    if (!c.mine) return;
-    const int64_t jg = (int64_t)j * c.g * c.plane;
-    {   // known slice j -> output slice j*g, bit-exact
-        TO kv[4];
-        const TI* cptr = lo + (lrow + R) * RP + PAD + lcol;
+    TO kv[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(cptr[p], c.scale);
-        if (!dry) st4<TO>(c.out + jg, kv, c.vec_out, c.nvalid);
-        if (c.var) {
-            const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-            st4<float>(c.var + jg, z4, c.vec_out, c.nvalid);
-        }
-        if (j == c.jlast) {  // the volume's last known slice
-            const TI* ch_ = hi + (lrow + R) * RP + PAD + lcol;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) kv[p] = (TO)cvt_out(ch_[p], c.scale);
-            const int64_t jg1 = jg + (int64_t)c.g * c.plane;
-            if (!dry) st4<TO>(c.out + jg1, kv, c.vec_out, c.nvalid);
-            if (c.var) {
-                const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-                st4<float>(c.var + jg1, z4, c.vec_out, c.nvalid);
-            }
-        }
+    for (int p = 0; p < 4; ++p) kv[p] = sizeof(TI) == 2 ? (TO)__fmul_rn((float)orb[p][0], c.scale) : (TO)orb[p][0];
+    st4<TO>(c.out + off, kv, c.vec_out, c.nvalid);
+    if (c.var) {
+        const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+        st4<float>(c.var + off, z4, c.vec_out, c.nvalid);
     }
-    if constexpr (GM1 == 0) {
-        return;
+}
+
+// Interpolated output slice t (1 <= t < g) of gap j for the interior pixels of
+// the four (and their kriging variance).
+template <typename TI>
+__device__ __forceinline__ void ds_store_t(const DsCtx<TI>& c, int64_t jg, int t, const typename DsTypes<TI>::TC (&acc)[KRIG_PX][2],
+                                           int i)
+{
+    typedef typename DsTypes<TI>::TO TO;
+    const int64_t off = jg + (int64_t)t * c.plane;
+    if (c.full) {
+        TO o[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][i];
+        st4<TO>(c.out + off, o, true, 4);
     } else {
-        if (!c.inner) return;  // no interior pixel among the four
-        TC acc[KRIG_PX][DsGP<GM1>::N];
 #pragma unroll
-        for (int p = 0; p < KRIG_PX; ++p)
-#pragma unroll
-            for (int t = 0; t < DsGP<GM1>::N; ++t) acc[p][t] = TC(0);
-        ds_accum_interior<TI, R, GM1>(acc, lo, hi, lrow, lcol, ow);
-        if (dry) return;  // warm-up pass: no stores
-        // the g-1 output slices of the gap, one branch for the whole set
+        for (int p = 0; p < 4; ++p)
+            if (p >= c.plo && p < c.phi) c.out[off + p] = (TO)acc[p][i];
+    }
+    if (c.var) {
+        const float vv = c.vt[t - 1];
         if (c.full) {
-#pragma unroll
-            for (int t = 0; t < GM1; ++t) {
-                TO o[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][t];
-                st4<TO>(c.out + jg + (int64_t)(t + 1) * c.plane, o, true, 4);
-            }
+            const float v4[4] = {vv, vv, vv, vv};
+            st4<float>(c.var + off, v4, true, 4);
         } else {
-#pragma unroll
-            for (int t = 0; t < GM1; ++t)
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    if (p >= c.plo && p < c.phi) c.out[jg + (int64_t)(t + 1) * c.plane + p] = (TO)acc[p][t];
-        }
-        if (c.var) {
-#pragma unroll
-            for (int t = 0; t < GM1; ++t) {
-                const float vv = c.vt[t];
-                const int64_t off = jg + (int64_t)(t + 1) * c.plane;
-                if (c.full) {
-                    const float v4[4] = {vv, vv, vv, vv};
-                    st4<float>(c.var + off, v4, true, 4);
-                } else {
-                    for (int p = c.plo; p < c.phi; ++p) c.var[off + p] = vv;
-                }
-            }
+            for (int p = c.plo; p < c.phi; ++p) c.var[off + p] = vv;
         }
     }
 }
 
-// Frame unit: 32 frame pixels of one gap, one lane each, full weight row of
-// the pixel's own truncation class; taps read from global memory (L2).
-__device__ __forceinline__ void ds_frame_pixel(const KrigVol& V, int f, int* x, int* y)
+// One item for one consumer warp: its 8 x 16 pixel block of the tile, every
+// gap of the item's chunk.  Each known slice's orbit sums are computed once,
+// right after its slot fills, and the slot is released at once (the sums stay
+// in registers for the next gap).  dry: warm-up pass over the first gap, no
+// stores and no release (the slots stay full for the real pass).  Returns
+// false if a wait gave up.
+template <typename TI, int R, int GM1>
+__device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int q, int lrow, int lcol, int lane,
+                                        const typename DsTypes<TI>::TC* ow, bool dry)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    constexpr int S = DsStages<TI>::S;
+    constexpr int NO = DsNO<R>::N;
+    TI* slots = DsLayout<TI>::slots();
+    uint64_t* full = DsLayout<TI>::full();
+    uint64_t* empty = DsLayout<TI>::empty();
+    constexpr int stride = DsLayout<TI>::stride;
+    const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
+    const bool orbits = GM1 > 0 && c.inner;
+    TC lo[KRIG_PX][NO];
+    if (!mbar_wait(&full[q % S], (q / S) & 1, DS_WAIT_LIMIT)) return false;
+    if (orbits) ds_orbits<TI, R>(slots + (q % S) * stride, lrow, lcol, lo);
+    else ds_centres<TI, R>(slots + (q % S) * stride, lrow, lcol, lo);
+    __syncwarp();
+    if (lane == 0 && !dry) mbar_arrive(&empty[q % S]);
+    for (int m = 0; m + 1 < nsl; ++m) {
+        const int j = d.c0 + m, qh = q + m + 1;
+        const int64_t jg = (int64_t)j * c.g * c.plane;
+        if (c.mine && !dry) ds_passthrough<TI, R>(c, jg, lo);
+        TC hi[KRIG_PX][NO];
+        if (!mbar_wait(&full[qh % S], (qh / S) & 1, DS_WAIT_LIMIT)) return false;
+        if (orbits) ds_orbits<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
+        else ds_centres<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
+        __syncwarp();
+        if (lane == 0 && !dry) mbar_arrive(&empty[qh % S]);
+        if constexpr (GM1 > 0) {
+            if (orbits) {
+                // one target pair per iteration (not unrolled: keeps the weight loads
+                // and accumulators of one pair live at a time)
+#pragma unroll 1
+                for (int t0 = 0; t0 < GM1; t0 += 2) {
+                    TC acc[KRIG_PX][2];
+                    ds_fma_pair<TI, R, GM1>(acc, t0, lo, hi, ow);
+                    if (!dry) {
+                        ds_store_t<TI>(c, jg, t0 + 1, acc, 0);
+                        if (t0 + 1 < GM1) ds_store_t<TI>(c, jg, t0 + 2, acc, 1);
+                    }
+                }
+            }
+        }
+        if (j == c.jlast && c.mine && !dry) ds_passthrough<TI, R>(c, jg + (int64_t)c.g * c.plane, hi);
+#pragma unroll
+        for (int p = 0; p < KRIG_PX; ++p)
+#pragma unroll
+            for (int o = 0; o < NO; ++o) lo[p][o] = hi[p][o];
+    }
+    return true;
+}
+
+// The class solve may still be running (programmatic dependent launch): wait
+// for it to complete, then copy the interior orbit weights of all volumes,
+// now final, into shared memory; a named barrier over the consumer warps only
+// (the producer runs on).  Every consumer warp calls this exactly once: before
+// its first real item, or after its last run if it had none.
+template <typename TI>
+__device__ __noinline__ void ds_weights_ready(const unsigned char* ws, int nv, int dtype)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    TC* owsm = DsLayout<TI>::ow();
+    const DsVolS* tab = DsLayout<TI>::vols(nv);
+    constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
+    for (int e = threadIdx.x; e < nv * NW; e += DS_CONSUMERS * 32) {
+        const DsVolS& Vv = tab[e / NW];
+        owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(ws + Vv.otab_off))[e % NW] : TC(0);
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
+}
+
+struct DsRunArgs {
+    const unsigned char* ws;
+    uint32_t* status;
+    int nv, k0, k1, warp, lane;
+};
+
+// All items of one run (volumes order[k0..k1), one shape) for this block's
+// consumer warp; returns the slice sequence number after them, or -1 after a
+// wait that gave up.  One non-inlined instance per shape, so the call (and
+// its register saves) happens once per run, not once per item.
+template <typename TI, int R, int GM1>
+__device__ __noinline__ int ds_run_shape(const DsRunArgs a, const int8_t* order, int q)
+{
+    typedef typename DsTypes<TI>::TC TC;
+    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    const DsVolS* tab = DsLayout<TI>::vols(a.nv);
+    int* pending = DsLayout<TI>::pending(a.warp);
+    const int lrow = (a.warp >> 2) * 8 + (a.lane >> 2);
+    const int lcol = (a.warp & 3) * 16 + (a.lane & 3) * 4;
+    int k = a.k0;
+    const int hi = tab[order[a.k1 - 1]].item_end;
+    for (int it = ds_first_item(tab[order[a.k0]].item_begin); it < hi; it += gridDim.x) {
+        while (it >= tab[order[k]].item_end) ++k;
+        const int v = order[k];
+        const DsVolS& V = tab[v];
+        DsItem d;
+        if (!ds_decode(V, it, d)) continue;
+        if (*(volatile int*)DsLayout<TI>::abort_flag()) return -1;
+        const TC* ow = DsLayout<TI>::ow() + v * (2 * KRIG_NORB * KRIG_TSLOTS);
+        // First item of the warp: a warm-up pass over its first gap (the same code,
+        // no stores) while the class solve may still run, so the consumer code is
+        // cached when the weights arrive; only then the wait (ds_weights_ready).
+        for (int pass = *pending ? 0 : 1; pass < 2; ++pass) {
+            const bool dry = pass == 0;
+            if (!dry && *pending) {
+                ds_weights_ready<TI>(a.ws, a.nv, dtype);
+                *pending = 0;
+            }
+            const DsCtx<TI> c = ds_ctx<TI, R>(V, a.ws, d, lrow, lcol, dry);
+            if (!ds_item<TI, R, GM1>(c, d, q, lrow, lcol, a.lane, ow, dry)) return -1;
+        }
+        q += d.c1 - d.c0 + 1;
+    }
+    return q;
+}
+
+template <typename TI, int R>
+__device__ __forceinline__ int ds_run_g(int g, const DsRunArgs& a, const int8_t* order, int q)
+{
+    switch (g) {
+    case 1: return ds_run_shape<TI, R, 0>(a, order, q);
+    case 2: return ds_run_shape<TI, R, 1>(a, order, q);
+    case 3: return ds_run_shape<TI, R, 2>(a, order, q);
+    case 4: return ds_run_shape<TI, R, 3>(a, order, q);
+    case 5: return ds_run_shape<TI, R, 4>(a, order, q);
+    case 6: return ds_run_shape<TI, R, 5>(a, order, q);
+    case 7: return ds_run_shape<TI, R, 6>(a, order, q);
+    default: return ds_run_shape<TI, R, 7>(a, order, q);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Frame units: 32 frame pixels (within r of the slice border) of one gap, one
+// lane each, through the full weight row of the pixel's own truncation class.
+// Tap coordinates are clamped into the slice and truncated taps carry zero
+// weight in the class row, so every load is independent and in flight at once.
+// Units are handed out by a ticket counter: the frame warp takes them from the
+// start, the consumer warps join after their last item.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ds_frame_pixel(const DsVolS& V, int f, int* x, int* y)
 {
     const int r = V.r, W = V.W, H = V.H;
     if (V.cint < 0) {
@@ -646,16 +787,12 @@ __device__ __forceinline__ void ds_frame_pixel(const KrigVol& V, int f, int* x, 
     }
 }
 
-// Branch-free: tap coordinates are clamped into the slice and truncated taps
-// carry zero weight in the class row, so all 2(2R+1)^2 loads are independent
-// and in flight together.
 template <typename TI, int R, int GM1>
-__device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, int f0, int lane)
+__device__ __noinline__ void ds_frame_unit(const DsVolS& V, const unsigned char* ws, int j, int f0, int lane)
 {
     typedef typename DsTypes<TI>::TC TC;
     typedef typename DsTypes<TI>::TO TO;
     constexpr int N2R = 2 * R + 1, NTAP = 2 * N2R * N2R;
-    const KrigVol& V = P.vol[v];
     const int f = f0 + lane;
     if (f >= V.n_frame) return;
     int x, y;
@@ -663,8 +800,8 @@ __device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, in
     const int W = V.W, H = V.H, g = V.g;
     const int64_t plane = (int64_t)H * W;
     const int cy = V.ymap[krig_slot(y, H, R)], cx = V.xmap[krig_slot(x, W, R)];
-    const TC* wrow = (const TC*)(P.ws + V.wtab_off) + ((int64_t)cy * V.ncx + cx) * NTAP * KRIG_TSLOTS;
-    const TI* in = (const TI*)P.in[v] + (size_t)j * plane;
+    const TC* wrow = (const TC*)(ws + V.wtab_off) + ((int64_t)cy * V.ncx + cx) * NTAP * KRIG_TSLOTS;
+    const TI* in = (const TI*)V.in + (size_t)j * plane;
     TC z[NTAP];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -681,13 +818,27 @@ __device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, in
 #pragma unroll
     for (int k = 0; k < NTAP; ++k) {
         TC w[8];
-        ldgw8(wrow + k * KRIG_TSLOTS, w);
+        if constexpr (sizeof(TC) == 4) {
+            float4 a = __ldg((const float4*)(wrow + k * KRIG_TSLOTS));
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            if (GM1 > 4) {
+                float4 b = __ldg((const float4*)(wrow + k * KRIG_TSLOTS + 4));
+                w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < (GM1 + 1) / 2; ++q) {
+                double2 a = __ldg((const double2*)(wrow + k * KRIG_TSLOTS + 2 * q));
+                w[2 * q] = a.x;
+                w[2 * q + 1] = a.y;
+            }
+        }
 #pragma unroll
         for (int t = 0; t < GM1; ++t) acc[t] = fma(w[t], z[k], acc[t]);
     }
-    TO* out = (TO*)P.out[v];
-    float* var = P.var[v];
-    const float* vt = (const float*)(P.ws + V.vtab_off) + ((int64_t)cy * V.ncx + cx) * KRIG_TSLOTS;
+    TO* out = (TO*)V.out;
+    float* var = V.var;
+    const float* vt = (const float*)(ws + V.vtab_off) + ((int64_t)cy * V.ncx + cx) * KRIG_TSLOTS;
     const int64_t pix = (int64_t)y * W + x;
 #pragma unroll
     for (int t = 0; t < GM1; ++t) {
@@ -697,147 +848,56 @@ __device__ __noinline__ void ds_frame_unit(const KrigLaunch& P, int v, int j, in
 }
 
 template <typename TI, int GM1>
-__device__ __forceinline__ void ds_frame_r(const KrigLaunch& P, int v, int j, int f0, int lane)
+__device__ __forceinline__ void ds_frame_r(const DsVolS& V, const unsigned char* ws, int j, int f0, int lane)
 {
-    switch (P.vol[v].r) {
-    case 0: ds_frame_unit<TI, 0, GM1>(P, v, j, f0, lane); break;
-    case 1: ds_frame_unit<TI, 1, GM1>(P, v, j, f0, lane); break;
-    default: ds_frame_unit<TI, 2, GM1>(P, v, j, f0, lane); break;
+    switch (V.r) {
+    case 0: ds_frame_unit<TI, 0, GM1>(V, ws, j, f0, lane); break;
+    case 1: ds_frame_unit<TI, 1, GM1>(V, ws, j, f0, lane); break;
+    default: ds_frame_unit<TI, 2, GM1>(V, ws, j, f0, lane); break;
     }
 }
 
 template <typename TI>
-__device__ __forceinline__ void ds_frame_dispatch(const KrigLaunch& P, int v, int j, int f0, int lane)
+__device__ __noinline__ void ds_frames(const unsigned char* ws, int nv, int dtype, int total, int lane)
 {
-    switch (P.vol[v].g) {
-    case 2: ds_frame_r<TI, 1>(P, v, j, f0, lane); break;
-    case 3: ds_frame_r<TI, 2>(P, v, j, f0, lane); break;
-    case 4: ds_frame_r<TI, 3>(P, v, j, f0, lane); break;
-    case 5: ds_frame_r<TI, 4>(P, v, j, f0, lane); break;
-    case 6: ds_frame_r<TI, 5>(P, v, j, f0, lane); break;
-    case 7: ds_frame_r<TI, 6>(P, v, j, f0, lane); break;
-    case 8: ds_frame_r<TI, 7>(P, v, j, f0, lane); break;
-    default: break;  // g = 1: nothing to interpolate
-    }
-}
-
-template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_consume_item(const KrigLaunch& P, const DsVolR<TI>& VR, const DsItem& d, int q,
-                                                TI* slots, int stride, const DsShared& sh, int warp, int lane, bool dry)
-{
-    constexpr int DS_STAGES = DsStages<TI>::S;
-    typedef typename DsTypes<TI>::TC TC;
-    // interior orbit weights of the item's volume
-    const TC* ow = (const TC*)sh.ow + d.v * (2 * KRIG_NORB * KRIG_TSLOTS);  // shared memory
-    const int lrow = (warp >> 2) * 8 + (lane >> 2);
-    const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
-    const DsCtx<TI> ctx = ds_ctx<TI, R>(VR, d, lrow, lcol, dry);
-    const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
-    bool ok = mbar_wait(&sh.full[q % DS_STAGES], (q / DS_STAGES) & 1, DS_WAIT_LIMIT);
-    for (int m = 0; m + 1 < nsl && ok; ++m) {
-        const int ql = q + m, qh = q + m + 1;
-        ok = mbar_wait(&sh.full[qh % DS_STAGES], (qh / DS_STAGES) & 1, DS_WAIT_LIMIT);
-        if (!ok) break;
-        ds_gap<TI, R, GM1>(ctx, d.c0 + m, slots + (ql % DS_STAGES) * stride, slots + (qh % DS_STAGES) * stride, lrow,
-                           lcol, ow, dry);
-        __syncwarp();
-        if (lane == 0 && !dry) mbar_arrive(&sh.empty[ql % DS_STAGES]);
-    }
-    __syncwarp();
-    if (dry) return;  // slots stay full, status untouched
-    if (ok) {
-        if (lane == 0) mbar_arrive(&sh.empty[(q + nsl - 1) % DS_STAGES]);
-    } else {
-        if (lane == 0) {
-            krig_set_status(P.status, KRIG_DEV_TIMEOUT);
-            atomicExch(sh.abort, 1);
+    const DsVolS* tab = DsLayout<TI>::vols(nv);
+    unsigned* ticket = (unsigned*)(ws + KRIG_CTRL_FRAME_NEXT) + dtype;
+    int v = 0;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = (int)atomicAdd(ticket, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) return;
+        // the volume of this input type whose frame units contain u (tickets rise, so search on from the last)
+        if (!(tab[v].dtype == dtype && u >= tab[v].frame_begin && u < tab[v].frame_end)) {
+            v = 0;
+            while (v < nv && !(tab[v].dtype == dtype && u >= tab[v].frame_begin && u < tab[v].frame_end)) ++v;
+            if (v >= nv) return;  // cannot happen: the units of this type are numbered contiguously
+        }
+        const DsVolS& V = tab[v];
+        const int lu = u - V.frame_begin;
+        const int j = lu / V.frame_units;
+        const int f0 = (lu - j * V.frame_units) * 32;
+        switch (V.g) {
+        case 2: ds_frame_r<TI, 1>(V, ws, j, f0, lane); break;
+        case 3: ds_frame_r<TI, 2>(V, ws, j, f0, lane); break;
+        case 4: ds_frame_r<TI, 3>(V, ws, j, f0, lane); break;
+        case 5: ds_frame_r<TI, 4>(V, ws, j, f0, lane); break;
+        case 6: ds_frame_r<TI, 5>(V, ws, j, f0, lane); break;
+        case 7: ds_frame_r<TI, 6>(V, ws, j, f0, lane); break;
+        case 8: ds_frame_r<TI, 7>(V, ws, j, f0, lane); break;
+        default: break;  // g = 1: no frame units
         }
     }
 }
 
-// All items of one shape for this block, in its order; returns the slice
-// sequence number after them.  One non-inlined instance per shape, so the
-// call (and its register saves) happens once per block, not once per item.
-// dry: warm-up pass over the first gap of the block's first item -- the same
-// instructions with no stores and no slot release, run while the class solve
-// is still going, so that the code is in the instruction caches when the
-// real pass starts (it is cold after the L2 has been flushed).
-// The class solve may still be running (programmatic dependent launch): wait
-// for it to complete, then copy the interior orbit weights of all volumes,
-// now final, into shared memory; a named barrier over the consumer warps only
-// (the producer runs on).  Every consumer warp calls this exactly once: before
-// its first real item, or after its last shape if it had none.
+// ---------------------------------------------------------------------------
+// Producer: streams every known slice of the block's items, in the consumers'
+// order, into the ring.
+// ---------------------------------------------------------------------------
 template <typename TI>
-__device__ __noinline__ void ds_weights_ready(const KrigLaunch& P, int dtype)
-{
-    typedef typename DsTypes<TI>::TC TC;
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    TC* owsm = (TC*)DsLayout<TI>::shared().ow;
-    const int nv = P.n_vols;
-    constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
-    for (int e = threadIdx.x; e < nv * NW; e += DS_CONSUMERS * 32) {
-        const KrigVol& Vv = P.vol[e / NW];
-        owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(P.ws + Vv.otab_off))[e % NW] : TC(0);
-    }
-    asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
-}
-
-template <typename TI, int R, int GM1>
-__device__ __noinline__ int ds_run_shape(const KrigLaunch& P, int q, int warp, int lane, bool dry, bool* pending)
-{
-    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
-    const DsShared sh = DsLayout<TI>::shared();
-    const int n_vols = P.n_vols, n_items = (int)P.n_items;
-    DsVolR<TI>& VR = *DsLayout<TI>::volr(warp);
-    if (lane == 0) VR = ds_volr<TI>(P, 0, dtype, R * 8 + GM1);
-    __syncwarp();
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        int v = 0;
-        for (int u = 1; u < n_vols; ++u)
-            if (P.vol[u].item_begin <= it) v = u;
-        if (v != VR.v) {
-            __syncwarp();
-            if (lane == 0) VR = ds_volr<TI>(P, v, dtype, R * 8 + GM1);
-            __syncwarp();
-        }
-        DsItem d;
-        if (!VR.match || !ds_decode_r(VR, it, d)) continue;
-        if (*(volatile int*)sh.abort) break;
-        // First item of the warp: a warm-up pass over its first gap (same code, no
-        // stores) while the class solve may still run, so the consumer code is
-        // cached when the weights arrive; only then the wait (ds_weights_ready).
-        for (int pass = (!dry && *pending) ? 0 : 1; pass < 2; ++pass) {
-            if (pass == 1 && !dry && *pending) {
-                ds_weights_ready<TI>(P, dtype);
-                *pending = false;
-            }
-            ds_consume_item<TI, R, GM1>(P, VR, d, q, DsLayout<TI>::slots(), DsLayout<TI>::stride, sh, warp, lane,
-                                        dry || pass == 0);
-        }
-        if (dry) break;
-        q += d.c1 - d.c0 + 1;
-    }
-    return q;
-}
-
-template <typename TI, int R>
-__device__ __forceinline__ int ds_run_g(int g, const KrigLaunch& P, int q, int warp, int lane, bool dry, bool* pending)
-{
-    switch (g) {
-    case 1: return ds_run_shape<TI, R, 0>(P, q, warp, lane, dry, pending);
-    case 2: return ds_run_shape<TI, R, 1>(P, q, warp, lane, dry, pending);
-    case 3: return ds_run_shape<TI, R, 2>(P, q, warp, lane, dry, pending);
-    case 4: return ds_run_shape<TI, R, 3>(P, q, warp, lane, dry, pending);
-    case 5: return ds_run_shape<TI, R, 4>(P, q, warp, lane, dry, pending);
-    case 6: return ds_run_shape<TI, R, 5>(P, q, warp, lane, dry, pending);
-    case 7: return ds_run_shape<TI, R, 6>(P, q, warp, lane, dry, pending);
-    default: return ds_run_shape<TI, R, 7>(P, q, warp, lane, dry, pending);
-    }
-}
-
-template <typename TI>
-__device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in, const DsItem& d, int s, TI* slot,
-                                                 uint64_t* bar, int lane, const CUtensorMap* map)
+__device__ __forceinline__ void ds_produce_slice(const DsVolS& V, const DsItem& d, int s, TI* slot, uint64_t* bar,
+                                                 int lane, const CUtensorMap* map)
 {
     if (map) {
         // one tensor-map request per slice tile; rows and columns outside the
@@ -851,7 +911,7 @@ __device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in,
         return;
     }
     const int64_t plane = (int64_t)V.H * V.W;
-    const TI* src = in + (size_t)s * plane;
+    const TI* src = (const TI*)V.in + (size_t)s * plane;
     const bool bulk = (V.W % (16 / (int)sizeof(TI))) == 0;
     switch (V.r) {
     case 0:
@@ -869,111 +929,116 @@ __device__ __forceinline__ void ds_produce_slice(const KrigVol& V, const TI* in,
     }
 }
 
-// One kernel per input type (compiled in separate translation units); items
-// of volumes of another type are skipped.
 template <typename TI>
-__global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P,
-                                                          const __grid_constant__ DsTma T)
+__device__ __noinline__ void ds_producer(const DsTma& T, const int8_t* order, uint32_t* status, int nv, int lane)
 {
-    constexpr int DS_STAGES = DsStages<TI>::S;
+    constexpr int S = DsStages<TI>::S;
     constexpr int stride = DsLayout<TI>::stride;
     const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    const DsVolS* tab = DsLayout<TI>::vols(nv);
     TI* slots = DsLayout<TI>::slots();
-    const DsShared sh = DsLayout<TI>::shared();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < DS_STAGES) {
-        mbar_init(&sh.full[tid], 1);
-        mbar_init(&sh.empty[tid], DS_CONSUMERS);
-    }
-    if (tid == 0) {
-        mbar_init(sh.never, 1);
-        *sh.abort = 0;
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
-    const int n_items = (int)P.n_items;
-    const uint32_t shapes = ds_shape_mask(P, dtype);
-    if (warp == DS_PRODUCER) {
-        // ---------------- producer warp: the consumers' item order (shape by shape)
-        int q = 0;
-        bool ok = true;
-        for (int it = blockIdx.x, c = 0; c < DS_NSHAPE && ok; it += gridDim.x) {
-            if (it >= n_items || !((shapes >> c) & 1u)) {
-                ++c;
-                it = (int)blockIdx.x - (int)gridDim.x;
-                continue;
-            }
+    uint64_t* full = DsLayout<TI>::full();
+    uint64_t* empty = DsLayout<TI>::empty();
+    int* abort = DsLayout<TI>::abort_flag();
+    int q = 0;
+    bool ok = true;
+    for (int k0 = 0, k1 = 0; k0 < nv && ok; k0 = k1) {
+        if (!ds_run(order, tab, nv, dtype, k0, &k1)) continue;
+        int k = k0;
+        const int hi = tab[order[k1 - 1]].item_end;
+        for (int it = ds_first_item(tab[order[k0]].item_begin); it < hi && ok; it += gridDim.x) {
+            while (it >= tab[order[k]].item_end) ++k;
+            const int v = order[k];
+            const DsVolS& V = tab[v];
             DsItem d;
-            if (!ds_decode(P, it, dtype, c, d)) continue;
-            const KrigVol& V = P.vol[d.v];
+            if (!ds_decode(V, it, d)) continue;
+            const CUtensorMap* map = (v < KRIG_TMA_VOLS && T.valid[v]) ? &T.tm[v] : nullptr;
             for (int s = d.c0; s <= d.c1; ++s, ++q) {
-                const int slot = q % DS_STAGES;
-                if (q >= DS_STAGES && !mbar_wait(&sh.empty[slot], ((q / DS_STAGES) - 1) & 1, DS_WAIT_LIMIT)) {
+                const int slot = q % S;
+                if (q >= S && !mbar_wait(&empty[slot], ((q / S) - 1) & 1, DS_WAIT_LIMIT)) {
                     ok = false;
                     break;
                 }
-                if (*(volatile int*)sh.abort) {
+                if (*(volatile int*)abort) {
                     ok = false;
                     break;
                 }
                 fence_proxy_async_smem();
-                const CUtensorMap* map = (d.v < KRIG_TMA_VOLS && T.valid[d.v]) ? &T.tm[d.v] : nullptr;
-                ds_produce_slice<TI>(V, (const TI*)P.in[d.v], d, s, slots + slot * stride, &sh.full[slot], lane, map);
+                ds_produce_slice<TI>(V, d, s, slots + slot * stride, &full[slot], lane, map);
             }
         }
-        if (!ok) {
-            if (lane == 0) {
-                krig_set_status(P.status, KRIG_DEV_TIMEOUT);
-                atomicExch(sh.abort, 1);
-            }
-            // bounded wait for the copies still in flight (the last DS_STAGES issued)
-            for (int qq = max(0, q - DS_STAGES); qq < q; ++qq)
-                mbar_wait(&sh.full[qq % DS_STAGES], (qq / DS_STAGES) & 1, DS_WAIT_LIMIT);
+    }
+    if (!ok) {
+        if (lane == 0) {
+            krig_set_status(status, KRIG_DEV_TIMEOUT);
+            atomicExch(abort, 1);
         }
+        // bounded wait for the copies still in flight (the last S issued)
+        for (int qq = max(0, q - S); qq < q; ++qq) mbar_wait(&full[qq % S], (qq / S) & 1, DS_WAIT_LIMIT);
+    }
+}
+
+// One kernel per input type (compiled in separate translation units); volumes
+// of another type are skipped run by run.
+template <typename TI>
+__global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant__ KrigLaunch P,
+                                                          const __grid_constant__ DsTma T)
+{
+    constexpr int S = DsStages<TI>::S;
+    const int dtype = sizeof(TI) == 8 ? KRIG_F64 : sizeof(TI) == 4 ? KRIG_F32 : KRIG_U16;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nv = P.n_vols;
+    if (tid < S) {
+        mbar_init(&DsLayout<TI>::full()[tid], 1);
+        mbar_init(&DsLayout<TI>::empty()[tid], DS_CONSUMERS);
+    }
+    if (tid == 0) {
+        mbar_init(DsLayout<TI>::never(), 1);
+        *DsLayout<TI>::abort_flag() = 0;
+    }
+    if (tid < DS_CONSUMERS) *DsLayout<TI>::pending(tid) = 1;
+    ds_fill_vols(P, (DsVolS*)DsLayout<TI>::vols(nv));
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (warp == DS_PRODUCER) {
+        ds_producer<TI>(T, P.ds_order, P.status, nv, lane);
         return;
     }
     if (warp == DS_FRAMER) {
-        // The class solve may still be running (programmatic dependent launch):
-        // wait for it to complete before the first read of the weight tables.
-        // The producer warp streams input slices only and does not wait; the
-        // consumer warps wait in ds_weights_ready.
+        // the class solve may still be running (programmatic dependent launch):
+        // wait for it to complete before the first read of the weight tables
         asm volatile("griddepcontrol.wait;" ::: "memory");
-        // ---------------- frame warp: border pixels (within r of the slice
-        // edge, their own truncation classes), latency-bound reads through L2,
-        // beside the consumers' tiles
-        const int64_t nfu = P.n_frame_units;
-        for (int64_t u = blockIdx.x; u < nfu; u += gridDim.x) {
-            int v = 0;
-            for (int w = 1; w < P.n_vols; ++w)
-                if (P.vol[w].frame_begin <= u) v = w;
-            const KrigVol& V = P.vol[v];
-            if (V.dtype != dtype || V.frame_units == 0) continue;
-            const int64_t lu = u - V.frame_begin;
-            const int j = (int)(lu / V.frame_units);
-            const int f0 = (int)(lu % V.frame_units) * 32;
-            ds_frame_dispatch<TI>(P, v, j, f0, lane);
-        }
+        ds_frames<TI>(P.ws, nv, dtype, P.ds_frame_units[dtype], lane);
         return;
     }
     // ---------------- consumer warps
     if (P.fault_timeout && blockIdx.x == 0 && warp == 0) {
         // test hook: wait on a barrier nothing completes; the bounded wait gives up
-        if (!mbar_wait(sh.never, 0, 1u << 12) && lane == 0) {
+        if (!mbar_wait(DsLayout<TI>::never(), 0, 1u << 12) && lane == 0) {
             krig_set_status(P.status, KRIG_DEV_TIMEOUT);
-            atomicExch(sh.abort, 1);
+            atomicExch(DsLayout<TI>::abort_flag(), 1);
         }
     }
+    const DsVolS* tab = DsLayout<TI>::vols(nv);
     int q = 0;
-    bool pending = true;  // weights not yet waited for (ds_weights_ready)
-    for (int c = 0; c < DS_NSHAPE; ++c) {
-        if (!((shapes >> c) & 1u)) continue;
-        const int r = c / 8, g = c % 8 + 1;
-        if (r == 0) q = ds_run_g<TI, 0>(g, P, q, warp, lane, false, &pending);
-        else if (r == 1) q = ds_run_g<TI, 1>(g, P, q, warp, lane, false, &pending);
-        else q = ds_run_g<TI, 2>(g, P, q, warp, lane, false, &pending);
+    DsRunArgs a{P.ws, P.status, nv, 0, 0, warp, lane};
+    for (int k0 = 0, k1 = 0; k0 < nv && q >= 0; k0 = k1) {
+        if (!ds_run(P.ds_order, tab, nv, dtype, k0, &k1)) continue;
+        const DsVolS& V = tab[P.ds_order[k0]];
+        a.k0 = k0;
+        a.k1 = k1;
+        if (V.r == 0) q = ds_run_g<TI, 0>(V.g, a, P.ds_order, q);
+        else if (V.r == 1) q = ds_run_g<TI, 1>(V.g, a, P.ds_order, q);
+        else q = ds_run_g<TI, 2>(V.g, a, P.ds_order, q);
     }
-    if (pending) ds_weights_ready<TI>(P, dtype);  // no item: still one arrival at the barrier
-    (void)slots;
+    if (q < 0) {
+        if (lane == 0) {
+            krig_set_status(P.status, KRIG_DEV_TIMEOUT);
+            atomicExch(DsLayout<TI>::abort_flag(), 1);
+        }
+    }
+    if (*DsLayout<TI>::pending(warp)) ds_weights_ready<TI>(P.ws, nv, dtype);  // no item: still one arrival
+    ds_frames<TI>(P.ws, nv, dtype, P.ds_frame_units[dtype], lane);
 }
 
 template <typename TI>
@@ -983,7 +1048,7 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
     bool any = false;
     for (int v = 0; v < L.n_vols; ++v) any = any || L.vol[v].dtype == dtype;
     if (!any) return 0;
-    const size_t smem = DsLayout<TI>::bytes;
+    const size_t smem = DsLayout<TI>::bytes(L.n_vols);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ds_apply<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
@@ -994,6 +1059,7 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
     const int sms = krig_device_sm_count();
     int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     if (grid > L.n_items) grid = L.n_items;
+    if (grid < 1) grid = 1;
     // programmatic dependent launch: this grid may start while the class
     // solve before it on the stream is still running
     cudaLaunchConfig_t cfg = {};

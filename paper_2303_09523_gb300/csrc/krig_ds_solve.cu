@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     __shared__ double ev[ZEV];
 
     const int tid = threadIdx.x;
+    // the stencil's frame-unit tickets start from zero (it reads them after this grid completes)
+    if (blockIdx.x == 0 && tid < 3) ((unsigned*)(P.ws + KRIG_CTRL_FRAME_NEXT))[tid] = 0u;
     // let the stencil kernel launch now; it waits for this grid before it reads the tables
     asm volatile("griddepcontrol.launch_dependents;");
     const int64_t cls = blockIdx.x;

@@ -27,6 +27,9 @@
 // Byte offset in the (zeroed) workspace control block of the LOO forward
 // launch's block ticket counter (reset by the launch's last block).
 #define KRIG_CTRL_LOO_DONE 64
+// Byte offset in the control block of the DS stencil's frame-unit tickets, one
+// 32-bit counter per input type (krig_dtype), zeroed by the class solve.
+#define KRIG_CTRL_FRAME_NEXT 128
 
 // n / d for 0 <= n < 2^32 by one multiply-high with m = krig_udiv_magic(d):
 // m = ceil(2^64 / d), and floor(n m / 2^64) = floor(n / d) because the error
@@ -61,7 +64,8 @@ struct KrigVol {
     int32_t chunks;           // chunks per sub-block
     int32_t cint;             // interior xy-class index, or -1 if the slice is narrower than 2r+1
     int32_t n_frame;          // frame pixels (within r of the border) per slice (DS)
-    int64_t frame_begin;      // first DS frame unit (32 frame pixels of one gap) of this volume
+    int64_t frame_begin;      // first DS frame unit (32 frame pixels of one gap) of this volume, numbered
+                              // among the volumes of its input type
     int32_t frame_units;      // frame units per gap
     int32_t gq;               // (n-1) / k: gaps of the smaller sub-blocks
     int32_t grm;              // (n-1) % k: the first grm sub-blocks have one gap more
@@ -95,6 +99,8 @@ struct KrigLaunch {
     int64_t n_classes;          // xy-classes over all volumes
     int64_t n_vox;              // output voxels over all volumes
     int64_t n_frame_units;      // DS frame units over all volumes
+    int32_t ds_frame_units[3];  // DS frame units per input type (krig_dtype)
+    int8_t ds_order[KRIG_MAX_VOLUMES];  // volumes in DS work-item order: by input type, then r, then g
     int32_t fault_timeout;      // test only: make one bounded device wait give up
     int32_t accumulate;         // LOO backward: add into grad_slices / grad_params
     int64_t n_loo_classes, n_loo_items, n_loo_adj;
@@ -255,6 +261,36 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     *off = up(*off + KRIG_LOO_REP * KRIG_NORB * 8);
     V.lvg_off = *off;
     *off = up(*off + sizeof(krig_variogram));
+}
+
+// Number the DS work items volume by volume in ds_order -- sorted by input
+// type and stencil shape (r, g), so that the items of one kernel instance and
+// shape are one contiguous range -- and the frame units per input type.
+// Called whenever the item counts change (plan creation, a new chunk length).
+inline void krig_ds_order(KrigLaunch& L)
+{
+    int n = 0;
+    for (int dt = 0; dt < 3; ++dt)
+        for (int r = 0; r <= KRIG_RMAX; ++r)
+            for (int g = 1; g <= KRIG_GMAX; ++g)
+                for (int v = 0; v < L.n_vols; ++v)
+                    if (L.vol[v].dtype == dt && L.vol[v].r == r && L.vol[v].g == g) L.ds_order[n++] = (int8_t)v;
+    int64_t items = 0;
+    for (int k = 0; k < n; ++k) {
+        KrigVol& V = L.vol[L.ds_order[k]];
+        V.item_begin = items;
+        items += (int64_t)V.k * V.chunks * V.tiles_x * V.tiles_y;
+    }
+    L.n_items = items;
+    for (int dt = 0; dt < 3; ++dt) {
+        int64_t f = 0;
+        for (int v = 0; v < L.n_vols; ++v)
+            if (L.vol[v].dtype == dt) {
+                L.vol[v].frame_begin = f;
+                f += (int64_t)(L.vol[v].n - 1) * L.vol[v].frame_units;
+            }
+        L.ds_frame_units[dt] = (int32_t)f;
+    }
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times

@@ -94,6 +94,7 @@ extern "C" krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, co
     L.n_items = items;
     L.n_classes = classes;
     L.n_vox = vox;
+    krig_ds_order(L);
 
     void* scratch = nullptr;
     krig_status st = noalloc_scratch(&scratch);
