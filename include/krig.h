@@ -266,6 +266,64 @@ krig_status krig_interpolate_noalloc(const krig_volume_desc* desc, const void* d
 krig_status krig_empirical_variogram(const krig_volume_desc* desc, const void* d_slices, int32_t max_lag,
                                      double* d_sums, int64_t* h_counts, void* stream);
 
+/* Similarity metrics of Appendix D between ground-truth images G and
+ * reconstructed images R (the paper scores each slice cut from the
+ * reconstructed volume against its ground-truth image): for every image i of a
+ * stack of n_img images of H x W pixels,
+ *   d_out[8 i + 0] = RMSE = sqrt(1/(HW) sum (R - G)^2)
+ *   d_out[8 i + 1] = MI(G, R) = sum p_GR log2(p_GR / (p_G p_R))   (bits)
+ *   d_out[8 i + 2] = MI(G, G) = the entropy of G on its own value range
+ *   d_out[8 i + 3] = ED = |H(G) - H(R)| / H(G)
+ *   d_out[8 i + 4] = SSIM = (2 mx my + c1)(2 sxy + c2) / ((mx^2 + my^2 + c1)(sx^2 + sy^2 + c2))
+ *   d_out[8 i + 5..7] = H(G), H(R), H(G, R)
+ * Appendix D fixes neither the histogram nor the SSIM constants; here:
+ * 256 equal bins over the joint range [min(G,R), max(G,R)] of the pair (a
+ * value's bin floor((x - lo) / (hi - lo) * 256) in FP64, clamped to [0, 255];
+ * all values in bin 0 when hi = lo), logarithms base 2, population moments
+ * over the whole image, c1 = (0.01 L)^2, c2 = (0.03 L)^2, L = max(G) - min(G).
+ *   d_G, d_R: device float32 [n_img][H][W].  d_out: device float64 [n_img][8].
+ *   d_work: caller-owned device scratch, 256-byte aligned, at least
+ *           krig_similarity_workspace_bytes(n_img, H, W) bytes (partial sums
+ *           and the 256 x 256 joint histogram of every image).
+ * Sums in FP64.  Asynchronous on `stream`; no allocation.  Errors: KRIG_EINVAL,
+ * KRIG_EWORKSPACE (before any launch), KRIG_ECUDA. */
+size_t krig_similarity_workspace_bytes(int32_t n_img, int32_t H, int32_t W);
+krig_status krig_similarity(const float* d_G, const float* d_R, int32_t n_img, int32_t H, int32_t W, void* d_work,
+                            size_t work_bytes, double* d_out, void* stream);
+
+/* Marching cubes (Appendix C): the triangle mesh of the iso-surface v = iso of a
+ * volume (for instance a reconstructed stack), into a caller-owned device
+ * buffer.  Every cube of 2 x 2 x 2 neighbouring voxels is classified by which
+ * corners are inside (v > iso); the surface crosses each edge between an
+ * inside and an outside corner at the linear-interpolation point.  The paper
+ * prints no case table; the one used is generated from the cube's geometry
+ * (krig_marching_cubes_table): on each face the cut edges are joined in pairs,
+ * a face with two diagonal inside corners cutting each of them off alone (so
+ * neighbouring cubes agree and the surface is closed); the segments, directed
+ * with the inside corners on their right as seen from outside the cube, close
+ * into loops, and each loop is fanned into triangles from its vertex on the
+ * edge of smallest index.  Triangle normals (right-hand rule) point out of the
+ * inside region.
+ *   d_vol: device float32 [D][H][W] (x fastest), D, H, W >= 2.
+ *   d_tri: device float32 [max_tri][3 vertices][x, y, z] in voxel units (corner
+ *          (x, y, z) of the volume at (x, y, z)); nullable when max_tri = 0.
+ *   d_ntri: device int64, receives the number of triangles of the surface; only
+ *           the first max_tri are written (call with max_tri = 0 to size d_tri).
+ *   d_work: caller-owned device scratch, 256-byte aligned, at least
+ *           krig_marching_cubes_workspace_bytes(D, H, W) bytes (one byte per cube
+ *           and a count per block of 2048 cubes).
+ * Triangles are in cube order (x fastest), a cube's in table order: the output
+ * is deterministic.  Asynchronous on `stream`.  Errors: KRIG_EINVAL,
+ * KRIG_EWORKSPACE (before any launch), KRIG_ECUDA. */
+size_t krig_marching_cubes_workspace_bytes(int32_t D, int32_t H, int32_t W);
+krig_status krig_marching_cubes(const float* d_vol, int32_t D, int32_t H, int32_t W, float iso, float* d_tri,
+                                int64_t max_tri, int64_t* d_ntri, void* d_work, size_t work_bytes, void* stream);
+/* The generated case table: tri_out[256][16] edge indices, three per triangle,
+ * -1 after the last; ntri_out[256] triangles per case (either nullable).  Edge
+ * e joins cube corners (kEdge): 0-3 along x, 4-7 along y, 8-11 along z; corner
+ * i = dx + 2 dy + 4 dz.  Host only. */
+void krig_marching_cubes_table(int8_t* tri_out, uint8_t* ntri_out);
+
 /* Measure the device's fused multiply-add rate (GFLOP/s, 2 flops per FMA)
  * in FP32 (fp64 = 0) or FP64 (fp64 = 1) on the current device with a short
  * synchronous kernel.  Support routine: the roofline denominator for kernels

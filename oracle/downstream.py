@@ -383,3 +383,145 @@ def mean_median_deblur(img, window=16, rel_threshold=0.25, system=None):
     info["theta_before"] = th
     info["theta_after"] = new_th
     return f, info
+
+
+# ---------------------------------------------------------------------------
+# Appendix C: marching cubes
+# ---------------------------------------------------------------------------
+#
+# The paper describes the method (256 corner configurations of a cube, linear
+# interpolation along the cut edges) but prints no table.  The reading taken,
+# derived here from the cube's geometry for every configuration:
+#   * a corner is inside when its value is above the iso level;
+#   * on every face the cut edges are paired into segments: walking the face's
+#     boundary counter-clockwise as seen from outside the cube, each edge where
+#     the walk enters the inside is joined to the nearest edge after it where
+#     the walk leaves the inside (so a face with two diagonal inside corners
+#     cuts each of them off alone); the segment runs from the first to the second;
+#   * the segments close into loops (every cut edge begins one segment and ends
+#     another); each loop, started at its edge of smallest number, is cut into
+#     a fan of triangles (loop[0], loop[i], loop[i+1]), whose normals (right-hand
+#     rule) point out of the inside region;
+#   * cube corners are the voxels (x+dx, y+dy, z+dz), dx, dy, dz in {0, 1};
+#     edges are numbered by axis (x: 0-3, y: 4-7, z: 8-11) and, within an axis,
+#     by the two other offsets (for x edges dy + 2 dz, for y edges dx + 2 dz, for
+#     z edges dx + 2 dy); a vertex lies on its edge at the fraction
+#     t = (iso - v_low) / (v_high - v_low) from the lower corner;
+#   * cubes in memory order of the volume (x fastest), their triangles in loop
+#     order.
+
+def _mc_edges():
+    """The 12 edges as (lower corner offset, axis) with the numbering above."""
+    edges = []
+    for axis in range(3):
+        others = [a for a in range(3) if a != axis]
+        for k in range(4):
+            off = [0, 0, 0]
+            off[others[0]] = k & 1
+            off[others[1]] = k >> 1
+            edges.append((tuple(off), axis))
+    return edges
+
+
+def _mc_faces():
+    """Each face as its four corner offsets in counter-clockwise order seen from outside."""
+    faces = []
+    for axis in range(3):
+        for side in (0, 1):
+            n = np.zeros(3)
+            n[axis] = 1.0 if side else -1.0
+            corners = [c for c in np.ndindex(2, 2, 2) if c[axis] == side]
+            centre = np.mean(np.array(corners, dtype=float), axis=0)
+            u = np.zeros(3)
+            u[(axis + 1) % 3] = 1.0
+            v = np.cross(n, u)  # (u, v, n) right-handed: angles about n increase counter-clockwise
+            ang = [np.arctan2(np.dot(np.array(c) - centre, v), np.dot(np.array(c) - centre, u)) for c in corners]
+            faces.append([tuple(corners[i]) for i in np.argsort(ang)])
+    return faces
+
+
+_MC_CACHE = {}
+
+
+def mc_case_triangles(inside):
+    """Triangles (as triples of edge numbers) of one cube configuration; ``inside`` maps a corner
+    offset (dx, dy, dz) to True when it lies above the iso level."""
+    key = tuple(bool(inside[c]) for c in np.ndindex(2, 2, 2))
+    if key in _MC_CACHE:
+        return _MC_CACHE[key]
+    edges = _mc_edges()
+    eid = {}
+    for i, (off, axis) in enumerate(edges):
+        hi = list(off)
+        hi[axis] = 1
+        eid[frozenset([off, tuple(hi)])] = i
+    nxt = {}
+    for face in _mc_faces():
+        crossings = []  # (edge, leaving) walking counter-clockwise
+        for i in range(4):
+            a, b = face[i], face[(i + 1) % 4]
+            if inside[a] != inside[b]:
+                crossings.append((eid[frozenset([a, b])], inside[a] and not inside[b]))
+        for k, (e, leaving) in enumerate(crossings):
+            if leaving:
+                continue
+            j = k + 1
+            while not crossings[j % len(crossings)][1]:
+                j += 1
+            nxt[e] = crossings[j % len(crossings)][0]
+    tris, seen = [], set()
+    for e0 in sorted(nxt):
+        if e0 in seen:
+            continue
+        loop, e = [], e0
+        while e not in seen:
+            seen.add(e)
+            loop.append(e)
+            e = nxt[e]
+        tris += [(loop[0], loop[i], loop[i + 1]) for i in range(1, len(loop) - 1)]
+    _MC_CACHE[key] = tris
+    return tris
+
+
+def marching_cubes(vol, iso):
+    """Iso-surface triangles of a volume (D x H x W, z y x), as an array [n, 3, 3] of vertex (x, y, z)
+    coordinates in voxel units, float64."""
+    V = np.asarray(vol)
+    D, H, W = V.shape
+    edges = _mc_edges()
+    inside_all = V > iso
+    out = []
+    for z in range(D - 1):
+        for y in range(H - 1):
+            block = inside_all[z:z + 2, y:y + 2, :]
+            anyin = block.any(axis=(0, 1))
+            allin = block.all(axis=(0, 1))
+            act = anyin[:-1] | anyin[1:]
+            full = allin[:-1] & allin[1:]
+            for x in np.nonzero(act & ~full)[0]:
+                inside = {(dx, dy, dz): bool(inside_all[z + dz, y + dy, x + dx]) for dx, dy, dz in np.ndindex(2, 2, 2)}
+                for tri in mc_case_triangles(inside):
+                    verts = []
+                    for e in tri:
+                        off, axis = edges[e]
+                        va = float(V[z + off[2], y + off[1], x + off[0]])
+                        hi = list(off)
+                        hi[axis] = 1
+                        vb = float(V[z + hi[2], y + hi[1], x + hi[0]])
+                        t = (float(iso) - va) / (vb - va)
+                        p = [x + off[0], y + off[1], z + off[2]]
+                        p[axis] += t
+                        verts.append(p)
+                    out.append(verts)
+    return np.array(out, dtype=np.float64).reshape(-1, 3, 3)
+
+
+def mesh_signed_volume(tris):
+    """Volume enclosed by a closed triangle mesh (divergence theorem, sum of signed tetrahedra)."""
+    t = np.asarray(tris, dtype=np.float64)
+    return float(np.sum(np.einsum("ij,ij->i", t[:, 0], np.cross(t[:, 1], t[:, 2]))) / 6.0)
+
+
+def mesh_area(tris):
+    t = np.asarray(tris, dtype=np.float64)
+    return float(0.5 * np.sum(np.linalg.norm(np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0]), axis=1)))

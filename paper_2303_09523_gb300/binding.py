@@ -93,6 +93,17 @@ def lib(build_if_missing: bool = False):
     L.krig_empirical_variogram.argtypes = [ctypes.POINTER(VolumeDesc), vp, ctypes.c_int32, vp,
                                            ctypes.POINTER(ctypes.c_int64), vp]
     L.krig_empirical_variogram.restype = ctypes.c_int
+    L.krig_similarity_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.krig_similarity_workspace_bytes.restype = ctypes.c_size_t
+    L.krig_similarity.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, vp]
+    L.krig_similarity.restype = ctypes.c_int
+    L.krig_marching_cubes_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.krig_marching_cubes_workspace_bytes.restype = ctypes.c_size_t
+    L.krig_marching_cubes.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp,
+                                      ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
+    L.krig_marching_cubes.restype = ctypes.c_int
+    L.krig_marching_cubes_table.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_uint8)]
+    L.krig_marching_cubes_table.restype = None
     _lib = L
     return L
 
@@ -266,6 +277,68 @@ def empirical_variogram(slices, max_lag, in_scale=1.0, stream=None):
                                           ctypes.c_void_p(sums.data_ptr()),
                                           counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream(stream)))
     return sums, counts
+
+
+SIMILARITY_FIELDS = ("rmse", "mi", "mi_gg", "ed", "ssim", "h_g", "h_r", "h_gr")
+
+
+def similarity(G, R, stream=None):
+    """Appendix D metrics of every image pair of two device float32 stacks (n, H, W) (or single
+    images (H, W)): krig_similarity.  Returns a device float64 tensor [n, 8] in the order of
+    ``SIMILARITY_FIELDS``."""
+    import torch
+    if G.shape != R.shape or G.dtype != torch.float32 or R.dtype != torch.float32:
+        raise ValueError("G and R must be float32 tensors of one shape")
+    G3 = G.contiguous().reshape(-1, G.shape[-2], G.shape[-1])
+    R3 = R.contiguous().reshape(-1, R.shape[-2], R.shape[-1])
+    n, H, W = G3.shape
+    L = lib()
+    nb = L.krig_similarity_workspace_bytes(n, H, W)
+    work = torch.empty(max(int(nb), 256), dtype=torch.uint8, device=G.device)
+    out = torch.empty((n, 8), dtype=torch.float64, device=G.device)
+    _check(L.krig_similarity(ctypes.c_void_p(G3.data_ptr()), ctypes.c_void_p(R3.data_ptr()), n, H, W,
+                             ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.c_void_p(out.data_ptr()),
+                             _stream(stream)))
+    return out
+
+
+def marching_cubes(vol, iso, max_tri=None, stream=None):
+    """Iso-surface triangles of a device float32 volume (D, H, W): krig_marching_cubes.  Returns
+    (tri, n): tri a device float32 tensor [min(n, max_tri), 3, 3] of vertex (x, y, z), n the number of
+    triangles of the surface.  Without ``max_tri`` a first call with no output sizes the buffer."""
+    import torch
+    v = vol.contiguous()
+    if v.dtype != torch.float32 or v.dim() != 3:
+        raise ValueError("vol must be a float32 tensor (D, H, W)")
+    D, H, W = v.shape
+    L = lib()
+    nb = L.krig_marching_cubes_workspace_bytes(D, H, W)
+    work = torch.empty(max(int(nb), 256), dtype=torch.uint8, device=v.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=v.device)
+
+    def call(buf, m):
+        _check(L.krig_marching_cubes(ctypes.c_void_p(v.data_ptr()), D, H, W, float(iso),
+                                     None if buf is None else ctypes.c_void_p(buf.data_ptr()), int(m),
+                                     ctypes.c_void_p(cnt.data_ptr()), ctypes.c_void_p(work.data_ptr()), work.numel(),
+                                     _stream(stream)))
+
+    if max_tri is None:
+        call(None, 0)
+        max_tri = int(cnt.item())
+    tri = torch.empty((max(int(max_tri), 1), 3, 3), dtype=torch.float32, device=v.device)
+    call(tri, max_tri)
+    n = int(cnt.item())
+    return tri[:min(n, int(max_tri))], n
+
+
+def marching_cubes_table():
+    """The case table of the library (numpy int8 [256, 16], uint8 [256])."""
+    import numpy as np
+    tri = np.zeros((256, 16), dtype=np.int8)
+    nt = np.zeros(256, dtype=np.uint8)
+    lib().krig_marching_cubes_table(tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                    nt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return tri, nt
 
 
 def desc_for(slices_shape, zfactor, half_w, n_sub_blocks, dtype_code_, in_scale=1.0):

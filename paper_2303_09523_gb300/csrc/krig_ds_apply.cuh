@@ -17,7 +17,7 @@
 // instead of 25 taps; a slice's orbit sums serve both gaps it brackets.
 // Pixels within r of the slice border ("frame" pixels) take the general path
 // with the full weight row of their own class, in units of 32 handed out by a
-// ticket counter to the frame warp and, after their items, the consumer warps.
+// ticket counter to every warp once its slices or items are done.
 //
 // Items are numbered by input type and stencil shape (the host sorts the
 // volumes), so each block walks one contiguous range per shape, round-robin
@@ -38,17 +38,16 @@ template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; stati
 
 #define DS_CONSUMERS 8                      // consumer warps (tiles)
 #define DS_PRODUCER DS_CONSUMERS            // streams the known-slice tiles
-#define DS_FRAMER (DS_CONSUMERS + 1)        // border pixels (frame units)
-#define DS_BLOCK ((DS_CONSUMERS + 2) * 32)
+#define DS_BLOCK ((DS_CONSUMERS + 1) * 32)  // 9 warps, two blocks per SM
 #define DS_WAIT_LIMIT (1u << 22)
 
-// Ring depth per input type: enough slots that the producer runs many slices
-// ahead of the consumers (a DRAM round trip spans many short gaps), while the
-// ring plus the orbit-weight table of all volumes (24 KB, 48 KB for f64)
-// stays within about 100 KB of shared memory, so two blocks fit on an SM.
+// Ring depth per input type.  Slots are released as soon as a slice's orbit
+// sums are formed, so a few slices ahead suffice; a shallow ring leaves the
+// rest of the SM's 256 KB of L1 / shared memory to the L1 cache (measured: 6
+// float slots run the batch and brain stacks 4-9 % faster than 12).
 template <typename TI> struct DsStages;
-template <> struct DsStages<uint16_t> { static constexpr int S = 16; };
-template <> struct DsStages<float> { static constexpr int S = 12; };
+template <> struct DsStages<uint16_t> { static constexpr int S = 10; };
+template <> struct DsStages<float> { static constexpr int S = 6; };
 template <> struct DsStages<double> { static constexpr int S = 4; };
 
 // ---------------------------------------------------------------------------
@@ -323,7 +322,15 @@ template <typename TI> struct DsLayout {
     static constexpr size_t ow_off = (flag_off + 4 * (1 + DS_CONSUMERS) + 15) / 16 * 16;
     static constexpr size_t ow_per_vol = 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(TC);
     __host__ __device__ static constexpr size_t vol_off(int nv) { return ow_off + (size_t)nv * ow_per_vol; }
-    __host__ __device__ static constexpr size_t bytes(int nv) { return vol_off(nv) + (size_t)nv * sizeof(DsVolS); }
+    // per consumer thread, the orbit sums of the previous slice when they do not stay in
+    // registers (ds_lo_smem): [NORB][256 threads][4 pixels]
+    __host__ __device__ static constexpr size_t orb_off(int nv)
+    {
+        return (vol_off(nv) + (size_t)nv * sizeof(DsVolS) + 15) / 16 * 16;
+    }
+    static constexpr size_t orb_bytes = (size_t)KRIG_NORB * DS_CONSUMERS * 32 * KRIG_PX * sizeof(TC);
+    __host__ __device__ static constexpr size_t bytes(int nv) { return orb_off(nv) + orb_bytes; }
+    __device__ static __forceinline__ TC* orb(int nv) { return (TC*)(ds_smem + orb_off(nv)); }
     __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
     __device__ static __forceinline__ uint64_t* full() { return (uint64_t*)(ds_smem + bar_off); }
     __device__ static __forceinline__ uint64_t* empty() { return (uint64_t*)(ds_smem + bar_off) + S; }
@@ -624,17 +631,58 @@ __device__ __forceinline__ void ds_store_t(const DsCtx<TI>& c, int64_t jg, int t
 // in registers for the next gap).  dry: warm-up pass over the first gap, no
 // stores and no release (the slots stay full for the real pass).  Returns
 // false if a wait gave up.
+// Where the previous slice's orbit sums wait for the next gap: in registers,
+// or, for the larger windows (r = 2; r >= 1 in FP64), in the thread's own
+// shared-memory rows, so that they are not live while the next slice's sums are
+// formed (the consumer code is held to 96 registers).
+template <typename TI, int R> struct DsLoSmem { static constexpr bool V = R == 2 || (sizeof(TI) == 8 && R >= 1); };
+
+template <typename TC, int NO>
+__device__ __forceinline__ void ds_put_orbits(TC* base, const TC (&o)[KRIG_PX][NO])
+{
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+        TC* p = base + (size_t)k * (DS_CONSUMERS * 32 * KRIG_PX);
+        if constexpr (sizeof(TC) == 4) {
+            *(float4*)p = make_float4(o[0][k], o[1][k], o[2][k], o[3][k]);
+        } else {
+            *(double2*)p = make_double2(o[0][k], o[1][k]);
+            *(double2*)(p + 2) = make_double2(o[2][k], o[3][k]);
+        }
+    }
+}
+
+template <typename TC, int NO>
+__device__ __forceinline__ void ds_get_orbits(const TC* base, TC (&o)[KRIG_PX][NO])
+{
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+        TC v[4];
+        ld4(base + (size_t)k * (DS_CONSUMERS * 32 * KRIG_PX), v);
+#pragma unroll
+        for (int p = 0; p < KRIG_PX; ++p) o[p][k] = v[p];
+    }
+}
+
+// One item for one consumer warp: its 8 x 16 pixel block of the tile, every
+// gap of the item's chunk.  Each known slice's orbit sums are computed once,
+// right after its slot fills, and the slot is released at once (the sums are
+// kept for the next gap).  dry: warm-up pass over the first gap, no stores and
+// no release (the slots stay full for the real pass).  Returns false if a wait
+// gave up.
 template <typename TI, int R, int GM1>
 __device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int q, int lrow, int lcol, int lane,
-                                        const typename DsTypes<TI>::TC* ow, bool dry)
+                                        const typename DsTypes<TI>::TC* ow, int nv, bool dry)
 {
     typedef typename DsTypes<TI>::TC TC;
     constexpr int S = DsStages<TI>::S;
     constexpr int NO = DsNO<R>::N;
+    constexpr bool LS = DsLoSmem<TI, R>::V;
     TI* slots = DsLayout<TI>::slots();
     uint64_t* full = DsLayout<TI>::full();
     uint64_t* empty = DsLayout<TI>::empty();
     constexpr int stride = DsLayout<TI>::stride;
+    TC* lsm = DsLayout<TI>::orb(nv) + threadIdx.x * KRIG_PX;  // this thread's rows (consumers: tid < 256)
     const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
     const bool orbits = GM1 > 0 && c.inner;
     TC lo[KRIG_PX][NO];
@@ -643,21 +691,23 @@ __device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int
     else ds_centres<TI, R>(slots + (q % S) * stride, lrow, lcol, lo);
     __syncwarp();
     if (lane == 0 && !dry) mbar_arrive(&empty[q % S]);
+    if (LS) ds_put_orbits<TC, NO>(lsm, lo);
     for (int m = 0; m + 1 < nsl; ++m) {
         const int j = d.c0 + m, qh = q + m + 1;
         const int64_t jg = (int64_t)j * c.g * c.plane;
-        if (c.mine && !dry) ds_passthrough<TI, R>(c, jg, lo);
         TC hi[KRIG_PX][NO];
         if (!mbar_wait(&full[qh % S], (qh / S) & 1, DS_WAIT_LIMIT)) return false;
         if (orbits) ds_orbits<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
         else ds_centres<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
         __syncwarp();
         if (lane == 0 && !dry) mbar_arrive(&empty[qh % S]);
+        if (LS) ds_get_orbits<TC, NO>(lsm, lo);
+        if (c.mine && !dry) ds_passthrough<TI, R>(c, jg, lo);
         if constexpr (GM1 > 0) {
             if (orbits) {
-                // one target pair per iteration (not unrolled: keeps the weight loads
-                // and accumulators of one pair live at a time)
-#pragma unroll 1
+                // one target pair at a time: the accumulators and weights of one
+                // pair live beside the two slices' orbit sums
+#pragma unroll
                 for (int t0 = 0; t0 < GM1; t0 += 2) {
                     TC acc[KRIG_PX][2];
                     ds_fma_pair<TI, R, GM1>(acc, t0, lo, hi, ow);
@@ -669,10 +719,14 @@ __device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int
             }
         }
         if (j == c.jlast && c.mine && !dry) ds_passthrough<TI, R>(c, jg + (int64_t)c.g * c.plane, hi);
+        if (LS) {
+            ds_put_orbits<TC, NO>(lsm, hi);
+        } else {
 #pragma unroll
-        for (int p = 0; p < KRIG_PX; ++p)
+            for (int p = 0; p < KRIG_PX; ++p)
 #pragma unroll
-            for (int o = 0; o < NO; ++o) lo[p][o] = hi[p][o];
+                for (int o = 0; o < NO; ++o) lo[p][o] = hi[p][o];
+        }
     }
     return true;
 }
@@ -736,7 +790,7 @@ __device__ __noinline__ int ds_run_shape(const DsRunArgs a, const int8_t* order,
                 *pending = 0;
             }
             const DsCtx<TI> c = ds_ctx<TI, R>(V, a.ws, d, lrow, lcol, dry);
-            if (!ds_item<TI, R, GM1>(c, d, q, lrow, lcol, a.lane, ow, dry)) return -1;
+            if (!ds_item<TI, R, GM1>(c, d, q, lrow, lcol, a.lane, ow, a.nv, dry)) return -1;
         }
         q += d.c1 - d.c0 + 1;
     }
@@ -763,8 +817,8 @@ __device__ __forceinline__ int ds_run_g(int g, const DsRunArgs& a, const int8_t*
 // lane each, through the full weight row of the pixel's own truncation class.
 // Tap coordinates are clamped into the slice and truncated taps carry zero
 // weight in the class row, so every load is independent and in flight at once.
-// Units are handed out by a ticket counter: the frame warp takes them from the
-// start, the consumer warps join after their last item.
+// Units are handed out by a ticket counter to every warp of the block once it is
+// done with its slices (producer) or items (consumers).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void ds_frame_pixel(const DsVolS& V, int f, int* x, int* y)
 {
@@ -1002,11 +1056,8 @@ __global__ void __launch_bounds__(DS_BLOCK, 2) k_ds_apply(const __grid_constant_
     __syncthreads();
     if (warp == DS_PRODUCER) {
         ds_producer<TI>(T, P.ds_order, P.status, nv, lane);
-        return;
-    }
-    if (warp == DS_FRAMER) {
-        // the class solve may still be running (programmatic dependent launch):
-        // wait for it to complete before the first read of the weight tables
+        // then border pixels beside the consumers, once the class solve has completed
+        // (programmatic dependent launch: it may still be running)
         asm volatile("griddepcontrol.wait;" ::: "memory");
         ds_frames<TI>(P.ws, nv, dtype, P.ds_frame_units[dtype], lane);
         return;

@@ -161,3 +161,16 @@ def test_noalloc_rejects_what_plan_create_rejects(lib, bad, status):
     st = fn(ctypes.byref(vd), 256, 256, None, 256, 1, None)
     assert st == status == _create([d])[0]
     assert len(lib.krig_last_error()) > 0
+
+
+def test_similarity_rejects_before_any_launch(lib):
+    vp = ctypes.c_void_p
+    out = vp(256)
+    assert lib.krig_similarity(None, vp(256), 1, 4, 4, vp(256), 1 << 20, out, None) == binding.KRIG_EINVAL
+    assert lib.krig_similarity(vp(256), vp(256), 0, 4, 4, vp(256), 1 << 20, out, None) == binding.KRIG_EINVAL
+    assert lib.krig_similarity(vp(256), vp(256), 1, 0, 4, vp(256), 1 << 20, out, None) == binding.KRIG_EINVAL
+    need = lib.krig_similarity_workspace_bytes(3, 64, 64)
+    assert need >= 3 * 256 * 256 * 4
+    assert lib.krig_similarity(vp(256), vp(256), 3, 64, 64, vp(256), need - 1, out, None) == binding.KRIG_EWORKSPACE
+    assert lib.krig_similarity(vp(256), vp(256), 3, 64, 64, vp(264), need, out, None) == binding.KRIG_EWORKSPACE
+    assert lib.krig_similarity_workspace_bytes(0, 4, 4) == 0

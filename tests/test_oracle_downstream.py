@@ -185,3 +185,91 @@ def test_deblur_touches_only_pixels_next_to_edges():
     assert out.shape == G.shape and info["n_edge"] > 0
     changed = np.argwhere(out != G)
     assert len(changed) == 0 or info["changed"] > 0
+
+
+# --------------------------------------------------------------------------- marching cubes (Appendix C)
+
+def _edge_keys(tris):
+    """Directed edges of a triangle soup with vertices identified by their rounded coordinates."""
+    keys = np.round(np.asarray(tris), 9)
+    out = []
+    for t in keys:
+        v = [tuple(p) for p in t]
+        out += [(v[0], v[1]), (v[1], v[2]), (v[2], v[0])]
+    return out
+
+
+def _check_closed(tris):
+    """Every edge of a closed, consistently oriented surface is used once in each direction;
+    returns the Euler characteristic V - E + F."""
+    d = _edge_keys(tris)
+    cnt = {}
+    for a, b in d:
+        cnt[(a, b)] = cnt.get((a, b), 0) + 1
+    for (a, b), c in cnt.items():
+        assert c == 1 and cnt.get((b, a), 0) == 1
+    verts = {a for a, _ in d}
+    return len(verts) - len(d) // 2 + len(tris)
+
+
+def test_mc_plane_closed_form():
+    """v = x cut at 2.3: every vertex at x = 2.3 (0.3 of the way from x = 2, not 0.7), the area is
+    (H-1)(D-1), normals along -x (out of the region x > 2.3)."""
+    D, H, W = 5, 7, 6
+    z, y, x = np.mgrid[0:D, 0:H, 0:W].astype(np.float32)
+    iso = np.float32(2.3)
+    tris = ds.marching_cubes(x, iso)
+    assert np.all(tris[:, :, 0] == float(iso))
+    assert ds.mesh_area(tris) == pytest.approx((H - 1) * (D - 1), abs=1e-12)
+    n = np.cross(tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0])
+    assert np.all(n[:, 0] < 0) and np.allclose(n[:, 1:], 0.0)
+
+
+def test_mc_sphere_is_closed_genus_zero_with_its_volume():
+    z, y, x = np.mgrid[0:24, 0:26, 0:28].astype(np.float64)
+    r = 8.0
+    vol = (r - np.sqrt((x - 13.5) ** 2 + (y - 12.5) ** 2 + (z - 11.5) ** 2)).astype(np.float32)
+    tris = ds.marching_cubes(vol, np.float32(0.0))
+    assert _check_closed(tris) == 2
+    assert ds.mesh_signed_volume(tris) == pytest.approx(4 / 3 * np.pi * r ** 3, rel=0.02)
+    assert ds.mesh_area(tris) == pytest.approx(4 * np.pi * r * r, rel=0.02)
+
+
+def test_mc_torus_has_euler_characteristic_zero():
+    z, y, x = np.mgrid[0:16, 0:36, 0:36].astype(np.float64)
+    R, a = 10.0, 3.5
+    q = np.sqrt((x - 17.5) ** 2 + (y - 17.5) ** 2) - R
+    vol = (a - np.sqrt(q ** 2 + (z - 7.5) ** 2)).astype(np.float32)
+    tris = ds.marching_cubes(vol, np.float32(0.0))
+    assert _check_closed(tris) == 0
+    assert ds.mesh_signed_volume(tris) == pytest.approx(2 * np.pi ** 2 * R * a * a, rel=0.03)
+
+
+def test_mc_random_field_is_watertight():
+    """Random values (every corner configuration, ambiguous faces included) inside a border of
+    zeros: the surfaces are closed and consistently oriented."""
+    rng = np.random.default_rng(8)
+    vol = np.zeros((12, 13, 14), dtype=np.float32)
+    vol[1:-1, 1:-1, 1:-1] = rng.random((10, 11, 12)).astype(np.float32)
+    tris = ds.marching_cubes(vol, np.float32(0.5))
+    assert len(tris) > 500
+    # closed and consistently oriented: every edge is used as often in one direction as in the
+    # other (a fan diagonal that lies on a face shared by two cubes is used by both cubes)
+    cnt = {}
+    for a, b in _edge_keys(tris):
+        cnt[(a, b)] = cnt.get((a, b), 0) + 1
+    for (a, b), c in cnt.items():
+        assert cnt.get((b, a), 0) == c
+    assert ds.mesh_signed_volume(tris) > 0
+
+
+def test_mc_case_triangles_basic_cases():
+    corners = list(np.ndindex(2, 2, 2))
+    assert ds.mc_case_triangles({c: False for c in corners}) == []
+    assert ds.mc_case_triangles({c: True for c in corners}) == []
+    for c0 in corners:
+        tri = ds.mc_case_triangles({c: c == c0 for c in corners})
+        assert len(tri) == 1  # one corner cut off: the triangle on its three edges
+    for k in range(256):
+        tri = ds.mc_case_triangles({c: bool((k >> i) & 1) for i, c in enumerate(corners)})
+        assert len(tri) <= 5
