@@ -113,6 +113,24 @@ typedef struct {
 /*   KRIG_FLAG_LOO: also size the workspace for krig_loo_forward / krig_backward
  *   (DS form only; every volume needs n_known >= 3). */
 #define KRIG_FLAG_LOO 0x2u
+/*   Universal kriging (Appendix A with more than one predictor, one
+ *   unbiasedness constraint and Lagrange multiplier each; Sec. 4.1.2 names the
+ *   method universal kriging).  DS form only, every volume of the plan:
+ *     KRIG_FLAG_DRIFT_Z:   drift {1, z} (z along the stack);
+ *     KRIG_FLAG_DRIFT_XYZ: drift {1, x, y, z} (needs half_w >= 1, H, W >= 2);
+ *     KRIG_FLAG_SLABS4:    the window in four known slices, j-1 .. j+2, those
+ *                          that exist (the "64 neighbours" of Sec. 4.1.2 read
+ *                          as 4 slices x the in-plane window), instead of the
+ *                          bracketing pair j, j+1.
+ *   Either drift flag, or KRIG_FLAG_SLABS4 alone (constant drift: ordinary
+ *   kriging on four slices), selects the universal-kriging path: one FP64
+ *   class solve per geometry class (truncation, and which outer slices exist)
+ *   with all targets t of a gap, then the stencil with each class's weights.
+ *   The kriging variance is w'gamma0 + mu'f0.  Not combinable with
+ *   KRIG_FLAG_LOO, KRIG_FLAG_DS_FP64_SOLVE or KRIG_FLAG_FAULT_TIMEOUT. */
+#define KRIG_FLAG_DRIFT_Z 0x4u
+#define KRIG_FLAG_DRIFT_XYZ 0x8u
+#define KRIG_FLAG_SLABS4 0x10u
 
 #define KRIG_MAX_VOLUMES 64
 

@@ -21,6 +21,9 @@ FORMS = {"P64": FORM_P64, "PMX": FORM_PMX, "DS": FORM_DS}
 MODELS = {"spherical": SPHERICAL, "exponential": EXPONENTIAL}
 FLAG_DS_FP64_SOLVE = 0x1
 FLAG_LOO = 0x2
+FLAG_DRIFT_Z = 0x4
+FLAG_DRIFT_XYZ = 0x8
+FLAG_SLABS4 = 0x10
 FLAG_FAULT_TIMEOUT = 0x100
 MAX_VOLUMES = 64
 TIMING_KINDS = 4

@@ -132,8 +132,22 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         return fail(KRIG_EINVAL, "n_vols must be in [1, %d] (got %d)", KRIG_MAX_VOLUMES, n_vols);
     if (form != KRIG_FORM_P64 && form != KRIG_FORM_PMX && form != KRIG_FORM_DS)
         return fail(KRIG_EINVAL, "unknown form %d", (int)form);
-    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT | KRIG_FLAG_LOO;
+    const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT | KRIG_FLAG_LOO | KRIG_FLAG_DRIFT_Z |
+                                 KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4;
     if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
+    const uint32_t uk_flags = KRIG_FLAG_DRIFT_Z | KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4;
+    if (flags & uk_flags) {
+        if ((flags & KRIG_FLAG_DRIFT_Z) && (flags & KRIG_FLAG_DRIFT_XYZ))
+            return fail(KRIG_EINVAL, "KRIG_FLAG_DRIFT_Z and KRIG_FLAG_DRIFT_XYZ exclude each other");
+        if (form != KRIG_FORM_DS) return fail(KRIG_EUNSUPPORTED, "universal kriging needs the DS form");
+        if (flags & (KRIG_FLAG_LOO | KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT))
+            return fail(KRIG_EUNSUPPORTED, "universal kriging plans take no LOO, FP64-solve or test flag");
+        for (int i = 0; i < n_vols; ++i)
+            if ((flags & KRIG_FLAG_DRIFT_XYZ) && (vols[i].half_w < 1 || vols[i].H < 2 || vols[i].W < 2))
+                return fail(KRIG_EUNSUPPORTED,
+                            "volume %d: the drift {1, x, y, z} needs half_w >= 1 and H, W >= 2 (else x or y is "
+                            "constant over the window)", i);
+    }
     for (int i = 0; i < n_vols; ++i) {
         krig_status st = krig_internal_check_desc(vols[i], i);
         if (st != KRIG_OK) return st;
@@ -165,6 +179,14 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         L.n_loo_classes = lc;
         L.n_loo_items = li;
         L.n_loo_adj = la;
+    }
+    if (flags & (KRIG_FLAG_DRIFT_Z | KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4)) {
+        L.uk_drift = (flags & KRIG_FLAG_DRIFT_XYZ) ? 2 : ((flags & KRIG_FLAG_DRIFT_Z) ? 1 : 0);
+        L.uk_slabs = (flags & KRIG_FLAG_SLABS4) ? 4 : 2;
+        int64_t uc = 0, ui = 0;
+        for (int i = 0; i < n_vols; ++i) krig_fill_uk(L.vol[i], L.uk_slabs, &off, &uc, &ui);
+        L.n_uk_classes = uc;
+        L.n_uk_items = ui;
     }
     L.n_items = items;
     L.n_classes = classes;
@@ -221,7 +243,10 @@ krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void
     }
     L.vg = d_params;
     cudaStream_t st = (cudaStream_t)stream;
-    if (plan->form == KRIG_FORM_DS) {
+    if (L.uk_slabs) {
+        krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_uk(L, st); }, "universal kriging launch");
+        if (s != KRIG_OK) return s;
+    } else if (plan->form == KRIG_FORM_DS) {
         const int fp64 = (plan->flags & KRIG_FLAG_DS_FP64_SOLVE) ? 1 : 0;
         krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_ds_solve(L, fp64, st); }, "class solve launch");
         if (s != KRIG_OK) return s;

@@ -83,6 +83,12 @@ struct KrigVol {
     int64_t lacc_off;         // loss accumulators, KRIG_LOO_REP doubles
     int64_t lorb_off;         // interior class: sum r * (orbit sum of both slices), [KRIG_LOO_REP][NORB] doubles
     int64_t lvg_off;          // variogram the LOO weights were last solved for (krig_variogram)
+    // universal kriging (plans created with a drift or four-slab flag)
+    int64_t uk_cls_begin;     // first UK class block of this volume
+    int64_t uk_item_begin;    // first UK tile item (gap, tile)
+    int64_t uk_wtab_off;      // UK weights [npat][ncy][ncx][slabs][2r+1][2r+1][8] (f64 for f64 input, else f32)
+    int64_t uk_vtab_off;      // UK variance [npat][ncy][ncx][8] f32
+    int32_t uk_tiles_x, uk_tiles_y;
 };
 
 struct KrigLaunch {
@@ -104,6 +110,9 @@ struct KrigLaunch {
     int32_t fault_timeout;      // test only: make one bounded device wait give up
     int32_t accumulate;         // LOO backward: add into grad_slices / grad_params
     int64_t n_loo_classes, n_loo_items, n_loo_adj;
+    int32_t uk_drift;           // universal kriging drift: 0 {1}, 1 {1, z}, 2 {1, x, y, z}
+    int32_t uk_slabs;           // known slices per neighbourhood: 2, or 4 (0: DS / per-voxel forms)
+    int64_t n_uk_classes, n_uk_items;
     // per-call LOO arguments
     float* pred[KRIG_MAX_VOLUMES];
     float* grad_slices[KRIG_MAX_VOLUMES];
@@ -129,6 +138,7 @@ int krig_launch_ds_solve(const KrigLaunch& L, int solve_fp64, void* stream);
 int krig_launch_ds_apply(const KrigLaunch& L, const DsTma& T, void* stream);
 int krig_launch_voxel(const KrigLaunch& L, int form, void* stream);
 int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int want_grad_params, void* stream);
+int krig_launch_uk(const KrigLaunch& L, void* stream);
 int krig_device_sm_count();
 
 // Set the thread-local message returned by krig_last_error() (krig_api.cu).
@@ -291,6 +301,32 @@ inline void krig_ds_order(KrigLaunch& L)
             }
         L.ds_frame_units[dt] = (int32_t)f;
     }
+}
+
+// Universal kriging (Appendix A with a drift): tile of the UK stencil, and the
+// slab patterns of a gap -- with four slabs the first gap has no slice below
+// and the last none above (bit 0: slice j-1 missing, bit 1: slice j+2 missing).
+#define KRIG_UK_TX 32
+#define KRIG_UK_TY 16
+__host__ __device__ inline int krig_uk_npat(int slabs) { return slabs == 4 ? 4 : 1; }
+__host__ __device__ inline int krig_uk_terms(int drift) { return drift == 0 ? 1 : (drift == 1 ? 2 : 4); }
+
+// Tables of one volume for the UK path (plans with a drift or four slabs).
+inline void krig_fill_uk(KrigVol& V, int slabs, int64_t* off, int64_t* classes, int64_t* items)
+{
+    const auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+    const int64_t ncls = (int64_t)krig_uk_npat(slabs) * V.ncx * V.ncy;
+    const int64_t taps = (int64_t)slabs * (2 * V.r + 1) * (2 * V.r + 1);
+    V.uk_tiles_x = (V.W + KRIG_UK_TX - 1) / KRIG_UK_TX;
+    V.uk_tiles_y = (V.H + KRIG_UK_TY - 1) / KRIG_UK_TY;
+    V.uk_cls_begin = *classes;
+    if (V.g >= 2) *classes += ncls;
+    V.uk_item_begin = *items;
+    *items += (int64_t)(V.n - 1) * V.uk_tiles_x * V.uk_tiles_y;
+    V.uk_wtab_off = *off;
+    *off = up(*off + ncls * taps * KRIG_TSLOTS * (V.dtype == KRIG_F64 ? 8 : 4));
+    V.uk_vtab_off = *off;
+    *off = up(*off + ncls * KRIG_TSLOTS * 4);
 }
 
 // Gaps per DS work item: enough items to keep every SM busy several times
