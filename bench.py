@@ -309,30 +309,83 @@ class DsHarness:
 
     def e2e(self, steps):
         """Same step through the public API with the slices in pinned host memory and the output read
-        back to pinned host memory every step (copies inside the timed region)."""
+        back to pinned host memory every step (copies inside the timed region).  Steps are pipelined
+        over two sets of device buffers, each with its own captured graph of the one plan: step i+1's
+        slices go up (copy stream) while step i is interpolated (compute stream, the graphs run one
+        after the other, never overlapping on the plan's workspace) and step i-1's volumes come down
+        (second copy stream).  Returns (ms for the steps, H2D bytes per step, D2H bytes per step,
+        pure-copy ms per step measured alone)."""
         import torch
         pin_in = [h.pin_memory() for h in self.host]
-        pin_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outs]
+        pin_out = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in self.outs] for _ in range(2)]
+        ins = [self.ts, [torch.empty_like(t) for t in self.ts]]
+        outs = [self.outs, [torch.empty_like(o) for o in self.outs]]
+        graphs = [self.graph, self.plan.capture(ins[1], outs[1], self.params)]
+        s_in, s_comp, s_out = (torch.cuda.Stream(device=self.dev) for _ in range(3))
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        ev_in, ev_comp, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        for b in range(2):  # every buffer starts free
+            for e in (ev_comp[b], ev_out[b]):
+                e.record(self.stream)
 
-        def step():
-            for d, h in zip(self.ts, pin_in):
-                d.copy_(h, non_blocking=True)
-            self.replay()
-            for h, o in zip(pin_out, self.outs):
-                h.copy_(o, non_blocking=True)
+        def step(i):
+            b = i % 2
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev_comp[b])  # the graph that last read these inputs is done
+                for d, h in zip(ins[b], pin_in):
+                    d.copy_(h, non_blocking=True)
+                ev_in[b].record(s_in)
+            with torch.cuda.stream(s_comp):
+                s_comp.wait_event(ev_in[b])
+                s_comp.wait_event(ev_out[b])  # the outputs of this buffer have been read back
+                graphs[b].replay()
+                ev_comp[b].record(s_comp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_comp[b])
+                for h, o in zip(pin_out[b], outs[b]):
+                    h.copy_(o, non_blocking=True)
+                ev_out[b].record(s_out)
 
-        for _ in range(3):
-            step()
+        def run(n):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            for st in (s_in, s_comp, s_out):
+                st.wait_event(e0)
+            for i in range(n):
+                step(i)
+            for st in (s_in, s_comp, s_out):
+                self.stream.wait_stream(st)
+            e1.record(self.stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        run(3)
+        ms = run(steps)
+        bi = sum(h.numel() * h.element_size() for h in pin_in)
+        bo = sum(h.numel() * h.element_size() for h in pin_out[0])
+        # the copies alone (both directions concurrently, same buffers), for the copy bound
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(self.stream)
+        for st in (s_in, s_out):
+            st.wait_event(c0)
+        for i in range(steps):
+            with torch.cuda.stream(s_in):
+                for d, h in zip(ins[i % 2], pin_in):
+                    d.copy_(h, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                for h, o in zip(pin_out[i % 2], outs[i % 2]):
+                    h.copy_(o, non_blocking=True)
+        for st in (s_in, s_out):
+            self.stream.wait_stream(st)
+        c1.record(self.stream)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(self.stream)
-        for _ in range(steps):
-            step()
-        e1.record(self.stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), sum(h.numel() * h.element_size() for h in pin_in), \
-            sum(h.numel() * h.element_size() for h in pin_out)
+        # the second buffer set's outputs must equal the first's (same slices, same plan)
+        for a, b_ in zip(outs[0], outs[1]):
+            if not torch.equal(a, b_):
+                raise RuntimeError("pipelined e2e: the two buffer sets disagree")
+        return ms, bi, bo, c0.elapsed_time(c1) / steps
 
     def close(self):
         self.plan.close()
@@ -383,11 +436,14 @@ def measure_workload(wl_key, vols, wl_name, args, dev, stream, flush, world, dis
             torch.cuda.synchronize()
         clk.mark(wl_key + ":clock_pass", c0, time.perf_counter())
     if e2e:
-        e_ms, bi, bo = h.e2e(max(3, min(steps, 50)))
-        e_ms = max_over_ranks(e_ms, dist, dev)
         ne = max(3, min(steps, 50))
+        e_ms, bi, bo, copy_ms = h.e2e(ne)
+        e_ms = max_over_ranks(e_ms, dist, dev)
         res["e2e"] = {"value": whole_job_rate(h.n_missing, ne, world, e_ms), "unit": "voxels/s",
-                      "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e_ms / ne}
+                      "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e_ms / ne,
+                      "copy_only_ms_per_step": copy_ms, "frac_of_copy_bound": copy_ms / (e_ms / ne),
+                      "pipeline": "two buffer sets: H2D of step i+1, interpolation of step i and D2H of step "
+                                  "i-1 on three streams"}
     if cpu and not args.no_cpu:
         sample = oracle_sample(vols, target_s=args.cpu_s, seed=11)
         var = h.variances()
@@ -457,6 +513,8 @@ def main():
     ap.add_argument("--no-fit", action="store_true", help="use the default spine variogram instead of the LOO fit")
     ap.add_argument("--no-loo", action="store_true", help="skip the leave-one-slice-out fwd+bwd timing")
     ap.add_argument("--no-variogram", action="store_true", help="skip the empirical-variogram timing")
+    ap.add_argument("--no-downstream", action="store_true",
+                    help="skip universal kriging, marching cubes and the similarity metrics")
     ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
@@ -533,6 +591,11 @@ def main():
             extra["fwd_bwd"] = time_loo(args, dev, stream, flush, spine_fit, with_oracle=not args.no_cpu)
         if not args.no_variogram:
             extra["empirical_variogram"] = time_variogram(args, dev, stream, flush)
+        if not args.no_downstream:
+            extra["universal_kriging"] = time_uk(args, dev, stream, flush, with_oracle=not args.no_cpu)
+            extra["marching_cubes"] = time_mc(args, dev, stream, flush, with_oracle=not args.no_cpu)
+            extra["similarity_table1_analogue"] = similarity_table(args, dev, stream, flush,
+                                                                   with_oracle=not args.no_cpu)
         peaks = {"fp32_fma_gflops": binding.measure_fma_peak(False), "fp64_fma_gflops": binding.measure_fma_peak(True)}
         extra["alu_peaks_measured"] = peaks
         if "forms" in extra and "P64" in extra["forms"]:
@@ -651,6 +714,148 @@ def time_loo(args, dev, stream, flush, spine_fit, with_oracle=True):
         for k in ("grad_theta", "grad_slices"):
             out["err_vs_oracle"][k]["within"] = out["err_vs_oracle"][k]["max_rel_normwise"] <= TOL_GRAD
     return out
+
+
+def _graph_time(fn, steps, flush, stream):
+    """Average CUDA-event ms of fn() (launches on `stream`) over `steps` calls, L2 flushed before each."""
+    import torch
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def time_uk(args, dev, stream, flush, with_oracle=True):
+    """Universal kriging (drift {1, x, y, z}, four known slices) on the spine and brain stacks:
+    FP64 class solve + stencil replayed as a CUDA graph, error against orc_uk_voxels on a sample."""
+    import torch
+    from paper_2303_09523_gb300 import binding, phantoms
+    res = {}
+    for name, vol, count in (("spine", phantoms.spine(), 1500), ("brain", phantoms.brain(), 300)):
+        t = torch.from_numpy(np.ascontiguousarray(vol.slices)).to(dev)
+        code = binding.dtype_code(t.dtype)
+        d = binding.desc_for(tuple(t.shape), vol.zfactor, vol.half_w, vol.n_sub_blocks, code, vol.in_scale)
+        out = torch.empty((vol.n_out, vol.H, vol.W), dtype=binding.out_dtype(code), device=dev)
+        params = binding.variogram_tensor([vol.variogram()], device=dev)
+        plan = binding.Plan([d], form="DS", flags=binding.FLAG_DRIFT_XYZ | binding.FLAG_SLABS4, device=dev)
+        g = plan.capture([t], [out], params)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        plan.device_status()
+        ms = _graph_time(g.replay, max(5, min(args.steps, 50)), flush, stream)
+        r = {"value": vol.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms, "workload": vol.name,
+             "drift": "1, x, y, z", "slabs": 4, "points_per_voxel": 4 * (2 * vol.half_w + 1) ** 2}
+        if with_oracle:
+            import oracle
+            rng = np.random.default_rng(21)
+            idx = _sample_missing(vol, count, rng)
+            est, _ = oracle.uk_voxels(vol.values_f64(), vol.zfactor, vol.half_w, idx, slabs=4, drift="xyz",
+                                      **vol.variogram())
+            got = _gather(out, idx)
+            r["err_vs_oracle"] = {"max_abs": float(np.abs(got - est).max()),
+                                  "max_rel_normwise": float(np.abs(got - est).max() / np.abs(est).max()),
+                                  "voxels": count, "tolerance": TOL_INTENSITY}
+        res[name] = r
+        plan.close()
+    return res
+
+
+def time_mc(args, dev, stream, flush, with_oracle=True):
+    """Marching cubes (Appendix C) on the kriged brain stack (187 x 512 x 512) at iso 0.5: the three
+    kernels per call, triangles per call, the volume read once and the triangles written as the
+    algorithmic bytes; the triangles of a cropped sub-volume against the oracle."""
+    import torch
+    from paper_2303_09523_gb300 import binding, phantoms
+    vol = phantoms.brain()
+    t = torch.from_numpy(np.ascontiguousarray(vol.slices)).to(dev)
+    outs, _ = binding.krige([dict(slices=t, zfactor=vol.zfactor, half_w=vol.half_w, n_sub_blocks=vol.n_sub_blocks,
+                                  variogram=vol.variogram())])
+    v = outs[0]
+    iso = 0.5
+    tri, n = binding.marching_cubes(v, iso)
+    D, H, W = v.shape
+    L = binding.lib()
+    work = torch.empty(int(L.krig_marching_cubes_workspace_bytes(D, H, W)), dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    import ctypes
+
+    def call():
+        binding._check(L.krig_marching_cubes(ctypes.c_void_p(v.data_ptr()), D, H, W, iso, ctypes.c_void_p(tri.data_ptr()),
+                                             tri.shape[0], ctypes.c_void_p(cnt.data_ptr()),
+                                             ctypes.c_void_p(work.data_ptr()), work.numel(),
+                                             ctypes.c_void_p(stream.cuda_stream)))
+
+    for _ in range(3):
+        call()
+    ms = _graph_time(call, max(5, min(args.steps, 30)), flush, stream)
+    cubes = (D - 1) * (H - 1) * (W - 1)
+    abytes = D * H * W * 4 + n * 36
+    peak, kind = _peaks()
+    r = {"value": cubes / (ms * 1e-3), "unit": "cubes/s", "ms_per_call": ms, "triangles": n, "iso": iso,
+         "workload": vol.name + " kriged output",
+         "roofline": {"bound": "hbm", "achieved": abytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                      "frac": abytes / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": abytes,
+                      "peak_source": kind + " hbm_gbs"}}
+    if with_oracle:
+        from oracle import downstream
+        # a crop around a vertex of the surface (x, y, z of the middle triangle)
+        cx_, cy_, cz_ = (int(c) for c in tri[n // 2, 0].tolist()) if n else (W // 2, H // 2, D // 2)
+        z0, y0, x0 = (max(0, min(c - 16, m - 32)) for c, m in ((cz_, D), (cy_, H), (cx_, W)))
+        sub = v[z0:z0 + 32, y0:y0 + 32, x0:x0 + 32].contiguous()
+        exp = downstream.marching_cubes(sub.cpu().numpy(), np.float32(iso))
+        got, m = binding.marching_cubes(sub, iso)
+        gh = got.double().cpu().numpy()
+        r["crop_vs_oracle"] = {"triangles": m, "oracle_triangles": int(len(exp)),
+                               "max_abs_vertex_err": float(np.abs(gh - exp).max()) if len(exp) == m and m else None}
+    return r
+
+
+def similarity_table(args, dev, stream, flush, with_oracle=True):
+    """The analogue of the paper's Table 1 on the phantoms: RMSE, MI, ED and SSIM (Appendix D) of every
+    interpolated slice (DS kriging on the GPU) against the phantom's noise-free slice at that z,
+    computed by krig_similarity, averaged; a few slices checked against the oracle's metrics."""
+    import torch
+    from paper_2303_09523_gb300 import binding, phantoms
+    res = {}
+    for name, mk in (("spine", phantoms.spine), ("brain", phantoms.brain)):
+        vol = mk(with_truth=True)
+        t = torch.from_numpy(np.ascontiguousarray(vol.slices)).to(dev)
+        outs, _ = binding.krige([dict(slices=t, zfactor=vol.zfactor, half_w=vol.half_w,
+                                      n_sub_blocks=vol.n_sub_blocks, variogram=vol.variogram(),
+                                      in_scale=vol.in_scale)])
+        miss = [z for z in range(vol.n_out) if z % vol.zfactor]
+        R = outs[0][miss].contiguous()
+        G = torch.from_numpy(vol.truth[miss].astype(np.float32)).to(dev)
+        m = binding.similarity(G, R)
+        ms = _graph_time(lambda: binding.similarity(G, R, stream=stream), 5, flush, stream)
+        mh = m.cpu().numpy()
+        varied = G.reshape(len(miss), -1).std(dim=1).cpu().numpy() > 0
+        row = {"images": len(miss), "ms_per_call": ms, "workload": vol.name,
+               "mean_rmse": float(mh[:, 0].mean()), "mean_mi": float(mh[:, 1].mean()),
+               "mean_mi_gg": float(mh[:, 2].mean()), "mean_ed": float(mh[:, 3].mean()),
+               "mean_ssim_anatomy_slices": float(mh[varied, 4].mean()) if varied.any() else None}
+        if with_oracle:
+            from oracle import downstream
+            errs = []
+            for i in (0, len(miss) // 2, len(miss) - 1):
+                Gi = G[i].double().cpu().numpy()
+                Ri = R[i].double().cpu().numpy()
+                lo, hi = downstream.joint_range(Gi, Ri)
+                exp = [downstream.rmse(Gi, Ri), downstream.mutual_information(Gi, Ri),
+                       downstream.mutual_information(Gi, Gi), downstream.entropy_difference(Gi, Ri),
+                       downstream.ssim_global(Gi, Ri)]
+                errs += [abs(mh[i, k] - exp[k]) / max(abs(exp[k]), 1e-12) for k in range(5) if np.isfinite(exp[k])]
+            row["max_rel_err_vs_oracle"] = float(max(errs))
+        res[name] = row
+    return res
 
 
 def emit(line, args):

@@ -12,9 +12,9 @@
 // FP64, clamped to [0, 255] (all zero when hi <= lo).
 //
 // Four launches per call: per-block partial sums and extrema, per-image
-// moments and ranges (and the histograms zeroed), the histograms (joint
-// 256 x 256 counts by global atomics, G's own-range counts in shared memory),
-// and per-image entropies and metrics.
+// means and ranges (and the histograms zeroed), the histograms (joint
+// 256 x 256 counts by global atomics, G's own-range counts in shared memory)
+// with the centred second moments, and per-image entropies and metrics.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -85,7 +85,8 @@ __device__ __forceinline__ T block_reduce(T v, T* red, bool is_max, bool is_min)
 }
 
 // Partial sums over one block's share of one image: sum G, R, G^2, R^2, GR,
-// (R - G)^2 in FP64 (products of the exact float values), min / max of G, R.
+// (R - G)^2 in FP64 (products of the exact float values), min / max of G, R
+// (the means and the ranges; the variances come from a second, centred pass).
 __global__ void __launch_bounds__(SIM_THREADS) k_sim_partial(const float* G, const float* R, int64_t npix, SimWork w)
 {
     __shared__ double red[SIM_THREADS / 32];
@@ -157,9 +158,12 @@ __device__ __forceinline__ int sim_bin(double x, double lo, double hi)
     return b < 0.0 ? 0 : (b > SIM_BINS - 1 ? SIM_BINS - 1 : (int)b);
 }
 
+// The histograms, and the centred sums sum (G - mx)^2, (R - my)^2, (G - mx)(R - my)
+// per block (two-pass moments: a constant image has exactly zero variance).
 __global__ void __launch_bounds__(SIM_THREADS) k_sim_hist(const float* G, const float* R, int64_t npix, SimWork w)
 {
     __shared__ unsigned own[SIM_BINS];
+    __shared__ double red[SIM_THREADS / 32];
     const int img = blockIdx.y, nb = gridDim.x;
     const double* st = w.stats + (size_t)img * SIM_STATS;
     const double lo = st[6], hi = st[7], glo = st[8], ghi = st[9];
@@ -168,19 +172,29 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_hist(const float* G, const 
     const float* g = G + (size_t)img * npix;
     const float* r = R + (size_t)img * npix;
     unsigned* joint = w.joint + (size_t)img * SIM_BINS * SIM_BINS;
+    const double mx = st[0] / st[10], my = st[1] / st[10];
+    double c[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)SIM_THREADS + threadIdx.x; i < npix; i += (int64_t)nb * SIM_THREADS) {
         const double a = g[i], b = r[i];
         atomicAdd(&joint[sim_bin(a, lo, hi) * SIM_BINS + sim_bin(b, lo, hi)], 1u);
         atomicAdd(&own[sim_bin(a, glo, ghi)], 1u);
+        c[0] += (a - mx) * (a - mx);
+        c[1] += (b - my) * (b - my);
+        c[2] += (a - mx) * (b - my);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < SIM_BINS; e += SIM_THREADS)
         if (own[e]) atomicAdd(&w.own[(size_t)img * SIM_BINS + e], own[e]);
+    double* out = w.part + ((size_t)img * nb + blockIdx.x) * SIM_PART;  // the first pass's partials are spent
+    for (int k = 0; k < 3; ++k) {
+        const double t = block_reduce<double>(c[k], red, false, false);
+        if (threadIdx.x == 0) out[k] = t;
+    }
 }
 
 // Per image: marginals, entropies and the metrics.  out[img][8] = rmse, mi,
 // mi_gg (= entropy of G on its own range), ed, ssim, h_g, h_r (joint binning), h_gr.
-__global__ void __launch_bounds__(SIM_THREADS) k_sim_final(SimWork w, double* out)
+__global__ void __launch_bounds__(SIM_THREADS) k_sim_final(SimWork w, int nb, double* out)
 {
     __shared__ double pg[SIM_BINS], pr[SIM_BINS];
     __shared__ double red[SIM_THREADS / 32];
@@ -218,7 +232,10 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_final(SimWork w, double* ou
     const double HGG = block_reduce<double>(hgg, red, false, false);
     if (t == 0) {
         const double mx = st[0] / n, my = st[1] / n;
-        const double vx = st[2] / n - mx * mx, vy = st[3] / n - my * my, cxy = st[4] / n - mx * my;
+        double cs[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < 3; ++k) cs[k] += w.part[((size_t)img * nb + b) * SIM_PART + k];
+        const double vx = cs[0] / n, vy = cs[1] / n, cxy = cs[2] / n;
         const double L = st[9] - st[8];
         const double c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
         double* o = out + (size_t)img * 8;
@@ -267,7 +284,7 @@ extern "C" krig_status krig_similarity(const float* d_G, const float* d_R, int32
     k_sim_partial<<<dim3(nb, n_img), SIM_THREADS, 0, st>>>(d_G, d_R, npix, w);
     k_sim_stats<<<n_img, SIM_THREADS, 0, st>>>(nb, npix, w);
     k_sim_hist<<<dim3(nb, n_img), SIM_THREADS, 0, st>>>(d_G, d_R, npix, w);
-    k_sim_final<<<n_img, SIM_THREADS, 0, st>>>(w, d_out);
+    k_sim_final<<<n_img, SIM_THREADS, 0, st>>>(w, nb, d_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sim_fail(KRIG_ECUDA, std::string("similarity launch: ") + cudaGetErrorString(e));
     return KRIG_OK;

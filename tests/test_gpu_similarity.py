@@ -85,3 +85,14 @@ def test_interpolated_spine_slices_against_truth():
         _check(got[i], Gh[i], Rh[i])
     varied = Gh.reshape(len(miss), -1).std(axis=1) > 0  # slices that cut the anatomy (others are background)
     assert varied.any() and np.median(got[varied, 4]) > 0.9
+
+
+def test_constant_ground_truth():
+    """A ground-truth slice that misses the anatomy is constant: zero variance and covariance exactly
+    (two-pass moments), entropy 0, as in the oracle."""
+    rng = np.random.default_rng(11)
+    G = np.full((64, 32), np.float32(0.1))
+    R = (0.1 + 0.01 * rng.normal(size=G.shape)).astype(np.float32)
+    got = _gpu(G, R)[0]
+    _check(got, G.astype(np.float64), R.astype(np.float64))
+    assert got[2] == 0.0 and got[5] == 0.0
