@@ -128,6 +128,12 @@ typedef struct {
  *   with all targets t of a gap, then the stencil with each class's weights.
  *   The kriging variance is w'gamma0 + mu'f0.  Not combinable with
  *   KRIG_FLAG_LOO, KRIG_FLAG_DS_FP64_SOLVE or KRIG_FLAG_FAULT_TIMEOUT. */
+/*   KRIG_FLAG_CLAMP_BLOCK_MINMAX: DS form (without drift flags) -- Algorithm 1
+ *   computes the maximum and minimum value of each block without saying what
+ *   they are for; with this flag every interpolated voxel is clamped to the
+ *   [min, max] of the known voxels of its Z sub-block (its known slices a_b ..
+ *   a_{b+1}, boundary slices included).  Off by default.  NaN estimates stay NaN. */
+#define KRIG_FLAG_CLAMP_BLOCK_MINMAX 0x20u
 #define KRIG_FLAG_DRIFT_Z 0x4u
 #define KRIG_FLAG_DRIFT_XYZ 0x8u
 #define KRIG_FLAG_SLABS4 0x10u

@@ -275,3 +275,30 @@ def empirical_variogram(slices, max_lag):
                 counts[s, dy + L, dx + L] = d.size
     return sums, counts
 
+
+
+def sub_blocks(n, k):
+    """Algorithm 1, step 2: the n - 1 gaps cut into k sub-blocks of whole gaps (the first (n-1) % k
+    blocks one gap longer); block b holds known slices a_b .. a_{b+1}.  Returns [a_0, ..., a_k]."""
+    q, rem = divmod(n - 1, k)
+    a = [0]
+    for b in range(k):
+        a.append(a[-1] + q + (1 if b < rem else 0))
+    return a
+
+
+def clamp_block_minmax(out, slices, g, k):
+    """The reading of Algorithm 1's per-block "maximum and minimum possible value": every missing
+    voxel of block b (output slices strictly between a_b g and a_{b+1} g) clamped to [min, max] of
+    the block's known slices a_b .. a_{b+1}.  Known slices are unchanged; NaN stays NaN."""
+    res = np.array(out, dtype=np.float64, copy=True)
+    S = np.asarray(slices, dtype=np.float64)
+    a = sub_blocks(S.shape[0], k)
+    for b in range(k):
+        lo = float(S[a[b]:a[b + 1] + 1].min())
+        hi = float(S[a[b]:a[b + 1] + 1].max())
+        for z in range(a[b] * g + 1, a[b + 1] * g):
+            if z % g:
+                blk = res[z]
+                res[z] = np.where(blk < lo, lo, np.where(blk > hi, hi, blk))
+    return res

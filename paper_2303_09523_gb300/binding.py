@@ -24,6 +24,7 @@ FLAG_LOO = 0x2
 FLAG_DRIFT_Z = 0x4
 FLAG_DRIFT_XYZ = 0x8
 FLAG_SLABS4 = 0x10
+FLAG_CLAMP_BLOCK_MINMAX = 0x20
 FLAG_FAULT_TIMEOUT = 0x100
 MAX_VOLUMES = 64
 TIMING_KINDS = 4

@@ -133,8 +133,11 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
     if (form != KRIG_FORM_P64 && form != KRIG_FORM_PMX && form != KRIG_FORM_DS)
         return fail(KRIG_EINVAL, "unknown form %d", (int)form);
     const uint32_t known_flags = KRIG_FLAG_DS_FP64_SOLVE | KRIG_FLAG_FAULT_TIMEOUT | KRIG_FLAG_LOO | KRIG_FLAG_DRIFT_Z |
-                                 KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4;
+                                 KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4 | KRIG_FLAG_CLAMP_BLOCK_MINMAX;
     if (flags & ~known_flags) return fail(KRIG_EINVAL, "unknown flag bits 0x%x", flags & ~known_flags);
+    if ((flags & KRIG_FLAG_CLAMP_BLOCK_MINMAX) &&
+        (form != KRIG_FORM_DS || (flags & (KRIG_FLAG_DRIFT_Z | KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4))))
+        return fail(KRIG_EUNSUPPORTED, "KRIG_FLAG_CLAMP_BLOCK_MINMAX applies to the DS form without drift flags");
     const uint32_t uk_flags = KRIG_FLAG_DRIFT_Z | KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4;
     if (flags & uk_flags) {
         if ((flags & KRIG_FLAG_DRIFT_Z) && (flags & KRIG_FLAG_DRIFT_XYZ))
@@ -179,6 +182,14 @@ krig_status krig_plan_create(krig_plan_t* plan, const krig_volume_desc* vols, in
         L.n_loo_classes = lc;
         L.n_loo_items = li;
         L.n_loo_adj = la;
+    }
+    if (flags & KRIG_FLAG_CLAMP_BLOCK_MINMAX) {
+        L.clamp = 1;
+        for (int i = 0; i < n_vols; ++i) {
+            L.vol[i].mm_off = off;
+            off = (off + 2LL * L.vol[i].k * (L.vol[i].dtype == KRIG_F64 ? 8 : 4) + 255) / 256 * 256;
+            L.n_mm_blocks += L.vol[i].k;
+        }
     }
     if (flags & (KRIG_FLAG_DRIFT_Z | KRIG_FLAG_DRIFT_XYZ | KRIG_FLAG_SLABS4)) {
         L.uk_drift = (flags & KRIG_FLAG_DRIFT_XYZ) ? 2 : ((flags & KRIG_FLAG_DRIFT_Z) ? 1 : 0);
@@ -248,6 +259,11 @@ krig_status krig_interpolate(krig_plan_t plan, const void* const* d_slices, void
         if (s != KRIG_OK) return s;
     } else if (plan->form == KRIG_FORM_DS) {
         const int fp64 = (plan->flags & KRIG_FLAG_DS_FP64_SOLVE) ? 1 : 0;
+        if (L.clamp) {
+            krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_block_minmax(L, st); },
+                                         "block min/max launch");
+            if (s != KRIG_OK) return s;
+        }
         krig_status s = timed_launch(plan, st, 0, [&] { return krig_launch_ds_solve(L, fp64, st); }, "class solve launch");
         if (s != KRIG_OK) return s;
         for (int v = 0; v < L.n_vols && v < KRIG_TMA_VOLS; ++v) {

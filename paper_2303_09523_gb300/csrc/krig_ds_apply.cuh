@@ -249,6 +249,7 @@ struct DsVolS {
     const void* in;
     void* out;
     float* var;
+    const void* mm;                // [k][2] min, max of each sub-block's known voxels, or null (no clamp)
     uint64_t mt, mc, mx;           // multiply-high divisors: tiles, chunks, tiles_x
     int64_t wtab_off, vtab_off, otab_off;
     int32_t item_begin, item_end;  // work items [begin, end)
@@ -260,7 +261,7 @@ struct DsVolS {
     float scale;
     int8_t xmap[(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
     int8_t ymap[(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
-    int8_t pad[2];
+    int8_t pad[10];
 };
 static_assert(sizeof(DsVolS) % 16 == 0, "DsVolS must keep 16-byte alignment of the table");
 
@@ -272,6 +273,7 @@ __device__ __forceinline__ void ds_fill_vols(const KrigLaunch& P, DsVolS* tab)
         s.in = P.in[v];
         s.out = P.out[v];
         s.var = P.var[v];
+        s.mm = P.clamp ? (const void*)(P.ws + V.mm_off) : nullptr;
         s.mt = V.mdiv_tiles;
         s.mc = V.mdiv_chunks;
         s.mx = V.mdiv_tx;
@@ -303,7 +305,7 @@ __device__ __forceinline__ void ds_fill_vols(const KrigLaunch& P, DsVolS* tab)
             s.xmap[i] = V.xmap[i];
             s.ymap[i] = V.ymap[i];
         }
-        s.pad[0] = s.pad[1] = 0;
+        for (int i = 0; i < 10; ++i) s.pad[i] = 0;
         tab[v] = s;
     }
 }
@@ -342,7 +344,7 @@ template <typename TI> struct DsLayout {
 };
 
 struct DsItem {
-    int c0, c1, x0, y0;
+    int c0, c1, x0, y0, b;  // gaps [c0, c1), tile origin, Z sub-block
 };
 
 // item -> (sub-block b, chunk ch, tile): item = (b * chunks + ch) * tiles + tile,
@@ -355,6 +357,7 @@ __device__ __forceinline__ bool ds_decode(const DsVolS& V, int it, DsItem& d)
     const uint32_t ty = krig_udiv(tile, V.mx), tx = tile - ty * (uint32_t)V.tiles_x;
     const int b = (int)bb;
     const int a0 = b * V.gq + min(b, V.grm), a1 = (b + 1) * V.gq + min(b + 1, V.grm);
+    d.b = b;
     d.c0 = a0 + (int)ch * V.chunk;
     d.c1 = min(d.c0 + V.chunk, a1);
     d.x0 = (int)tx * KRIG_TX;
@@ -551,6 +554,8 @@ struct DsCtx {
     float scale;
     int nvalid, plo, phi;           // valid pixels of the four; interior ones [plo, phi)
     bool mine, vec_out, inner, full;
+    bool clamp;                     // clamp the estimates to [lo, hi], the sub-block's known range
+    typename DsTypes<TI>::TC lo, hi;
 };
 
 template <typename TI, int R>
@@ -577,6 +582,13 @@ __device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolS& V, const unsigned char
     c.phi = min(c.nvalid, W - R - xb);
     c.inner = c.mine && V.cint >= 0 && y >= R && y <= H - 1 - R && c.plo < c.phi;
     c.full = c.vec_out && c.plo == 0 && c.phi == KRIG_PX;
+    c.clamp = V.mm != nullptr;
+    c.lo = c.hi = 0;
+    if (c.clamp) {
+        const typename DsTypes<TI>::TC* mm = (const typename DsTypes<TI>::TC*)V.mm + 2 * d.b;
+        c.lo = mm[0];
+        c.hi = mm[1];
+    }
     return c;
 }
 
@@ -711,6 +723,13 @@ __device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int
                 for (int t0 = 0; t0 < GM1; t0 += 2) {
                     TC acc[KRIG_PX][2];
                     ds_fma_pair<TI, R, GM1>(acc, t0, lo, hi, ow);
+                    if (c.clamp) {
+#pragma unroll
+                        for (int p = 0; p < KRIG_PX; ++p)
+#pragma unroll
+                            for (int i = 0; i < 2; ++i)  // comparisons keep a NaN (singular system) a NaN
+                                acc[p][i] = acc[p][i] < c.lo ? c.lo : (acc[p][i] > c.hi ? c.hi : acc[p][i]);
+                    }
                     if (!dry) {
                         ds_store_t<TI>(c, jg, t0 + 1, acc, 0);
                         if (t0 + 1 < GM1) ds_store_t<TI>(c, jg, t0 + 2, acc, 1);
@@ -889,6 +908,13 @@ __device__ __noinline__ void ds_frame_unit(const DsVolS& V, const unsigned char*
         }
 #pragma unroll
         for (int t = 0; t < GM1; ++t) acc[t] = fma(w[t], z[k], acc[t]);
+    }
+    if (V.mm) {  // the gap's sub-block: the first grm blocks have gq + 1 gaps
+        const int big = V.grm * (V.gq + 1);
+        const int b = j < big ? j / (V.gq + 1) : V.grm + (j - big) / V.gq;
+        const TC* mm = (const TC*)V.mm + 2 * b;
+#pragma unroll
+        for (int t = 0; t < GM1; ++t) acc[t] = acc[t] < mm[0] ? mm[0] : (acc[t] > mm[1] ? mm[1] : acc[t]);
     }
     TO* out = (TO*)V.out;
     float* var = V.var;

@@ -60,6 +60,7 @@ struct KrigVol {
     int64_t vtab_off;         // byte offset of the DS variance table in the workspace
     int64_t lag_off;          // byte offset of the FP64 lag tables (per-voxel forms)
     int64_t otab_off;         // byte offset of the interior-class orbit weights [2][6][8] (DS)
+    int64_t mm_off;           // byte offset of [k][2] known-value min / max per sub-block (clamp plans)
     int32_t chunk;            // gaps per DS work item (a sub-block is cut into chunks)
     int32_t chunks;           // chunks per sub-block
     int32_t cint;             // interior xy-class index, or -1 if the slice is narrower than 2r+1
@@ -110,6 +111,8 @@ struct KrigLaunch {
     int32_t fault_timeout;      // test only: make one bounded device wait give up
     int32_t accumulate;         // LOO backward: add into grad_slices / grad_params
     int64_t n_loo_classes, n_loo_items, n_loo_adj;
+    int32_t clamp;              // clamp DS estimates to their sub-block's known range
+    int64_t n_mm_blocks;        // sub-blocks over all volumes (clamp plans)
     int32_t uk_drift;           // universal kriging drift: 0 {1}, 1 {1, z}, 2 {1, x, y, z}
     int32_t uk_slabs;           // known slices per neighbourhood: 2, or 4 (0: DS / per-voxel forms)
     int64_t n_uk_classes, n_uk_items;
@@ -139,6 +142,7 @@ int krig_launch_ds_apply(const KrigLaunch& L, const DsTma& T, void* stream);
 int krig_launch_voxel(const KrigLaunch& L, int form, void* stream);
 int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int want_grad_params, void* stream);
 int krig_launch_uk(const KrigLaunch& L, void* stream);
+int krig_launch_block_minmax(const KrigLaunch& L, void* stream);
 int krig_device_sm_count();
 
 // Set the thread-local message returned by krig_last_error() (krig_api.cu).

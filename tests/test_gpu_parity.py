@@ -195,7 +195,8 @@ def test_spine_full_size_sampled(form):
     _check_sampled(phantoms.spine(), form)
 
 
-@pytest.mark.parametrize("form", ["DS", "PMX"])
+@pytest.mark.parametrize("form", ["DS", "PMX", "P64"])
 def test_brain_full_size_sampled(form):
-    """32 known 512x512 float32 slices, g 6 (187 slices), 8 sub-blocks, exponential, 50 points."""
+    """32 known 512x512 float32 slices, g 6 (187 slices), 8 sub-blocks, exponential, 50 points (the
+    plain FP64 form too: its warp-per-voxel 50-point solve at full size)."""
     _check_sampled(phantoms.brain(), form, count=8000)

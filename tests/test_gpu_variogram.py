@@ -50,6 +50,15 @@ def test_empirical_variogram_uint16_spine():
     _check(vol.values_f64(), t, 6, in_scale=vol.in_scale)
 
 
+def test_empirical_variogram_full_spine_at_the_benchmarked_lag():
+    """The benchmarked case: the whole spine stack (24 x 256 x 256 uint16), every lag vector up to 8
+    (8.6e8 voxel pairs, FP32 row sums then FP64), against the oracle."""
+    vol = phantoms.spine()
+    t = torch.from_numpy(np.ascontiguousarray(vol.slices)).cuda()
+    got, counts = _check(vol.values_f64(), t, 8, in_scale=vol.in_scale)
+    assert int(counts.sum()) == 860964800
+
+
 def test_empirical_variogram_rejects_bad_arguments():
     t = torch.zeros((3, 8, 8), dtype=torch.float32, device="cuda")
     with pytest.raises(binding.KrigError):

@@ -512,3 +512,35 @@ def test_uk_voxels_neighbourhood_is_the_stated_slab_window():
             est, var = oracle.uk_voxels(S, g, r, [[j * g + t, y, x]], slabs=slabs, drift="xyz", **vg)
             assert est[0] == pytest.approx(ref["est"], rel=1e-12, abs=1e-14)
             assert var[0] == pytest.approx(ref["var"], rel=1e-12)
+
+
+def test_sub_blocks_partition_the_gaps():
+    """Algorithm 1 step 2 as read: k blocks of whole gaps, the first (n-1) % k one gap longer."""
+    assert oracle.sub_blocks(24, 4) == [0, 6, 12, 18, 23]
+    assert oracle.sub_blocks(32, 8) == [0, 4, 8, 12, 16, 20, 24, 28, 31]
+    assert oracle.sub_blocks(9, 2) == [0, 4, 8]
+    assert oracle.sub_blocks(2, 1) == [0, 1]
+
+
+def test_clamp_block_minmax_hand_worked():
+    """Three known 1 x 2 slices, g = 2, two blocks: block 0 holds slices 0, 1 (range [0, 2]), block 1
+    slices 1, 2 (range [1, 5]); output slices 1 and 3 are the missing ones."""
+    S = np.array([[[0.0, 2.0]], [[1.0, 1.5]], [[5.0, 3.0]]])
+    out = np.array([[[0.0, 2.0]], [[-1.0, 2.5]], [[1.0, 1.5]], [[0.5, 7.0]], [[5.0, 3.0]]])
+    exp = np.array([[[0.0, 2.0]], [[0.0, 2.0]], [[1.0, 1.5]], [[1.0, 5.0]], [[5.0, 3.0]]])
+    assert np.array_equal(oracle.clamp_block_minmax(out, S, 2, 2), exp)
+    out[1, 0, 0] = np.nan
+    assert np.isnan(oracle.clamp_block_minmax(out, S, 2, 2)[1, 0, 0])
+
+
+def test_clamp_block_minmax_keeps_in_range_estimates_and_is_idempotent():
+    rng = np.random.default_rng(3)
+    S = rng.random((7, 9, 11))
+    out, _ = oracle.krige_volume(S, 3, 1, k_sub=3, model="spherical", nugget=0.0, sill=float(S.var()), range=8.0)
+    c = oracle.clamp_block_minmax(out, S, 3, 3)
+    assert np.array_equal(c[::3], S)
+    assert np.array_equal(oracle.clamp_block_minmax(c, S, 3, 3), c)
+    a = oracle.sub_blocks(7, 3)
+    for b in range(3):
+        blk = c[a[b] * 3:a[b + 1] * 3 + 1]
+        assert blk.min() >= S[a[b]:a[b + 1] + 1].min() and blk.max() <= S[a[b]:a[b + 1] + 1].max()
