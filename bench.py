@@ -909,7 +909,9 @@ def time_variogram(args, dev, stream, flush, max_lag=8):
     pairs = int(counts.sum())
     out = {"value": pairs / (ms * 1e-3), "unit": "voxel pairs/s", "ms_per_call": ms, "max_lag": max_lag,
            "lag_vectors": int(counts.size), "pairs_per_call": pairs, "workload": vol.name}
-    out["fit"] = variogram_fits(sums.cpu().numpy(), counts, vol)
+    # the fit uses the widest lags the kernel stages (16 pixels: distance classes to about 23 voxels)
+    sums16, counts16 = binding.empirical_variogram(s_dev, 16, in_scale=vol.in_scale, stream=stream)
+    out["fit"] = variogram_fits(sums16.cpu().numpy(), counts16, vol)
     return out
 
 
@@ -925,7 +927,8 @@ def variogram_fits(sums, counts, vol):
         res["wls"] = "unavailable: %s" % e
         return res
     nug, sill, rng = r["theta"]
-    res["wls"] = {"nugget": nug, "sill": sill, "range": rng, "classes": int(len(h)), "max_lag_length": float(h.max())}
+    res["wls"] = {"nugget": nug, "sill": sill, "range": rng, "classes": int(len(h)), "max_lag_length": float(h.max()),
+                  "range_at_bound": r["range_at_bound"], "max_lag": 16}
     return res
 
 

@@ -146,22 +146,29 @@ def variogram_model(h, model, nugget, sill, rng):
     return nugget + sill * (1.0 - np.exp(-3.0 * h / rng))
 
 
-def fit_variogram_wls(h, gamma, n, model, init=None):
+def fit_variogram_wls(h, gamma, n, model, init=None, max_range=None):
     """Weighted least squares: minimise sum_b n_b (gamma_b / gamma(h_b; theta) - 1)^2 over
-    theta = (nugget >= 0, partial sill > 0, range > 0).  Returns dict ``theta`` (nugget, sill, range)
-    and ``cost``."""
+    theta = (nugget >= 0, partial sill > 0, 0 < range <= max_range).  The data say nothing about a
+    range far beyond the longest lag class, where the models are all but linear in h (a fit that
+    runs off there trades range for sill along a ridge), so the range is bounded by default at three
+    times the longest class.  Returns dict ``theta`` (nugget, sill, range), ``cost`` and
+    ``range_at_bound`` (True when the bound holds the range: no sill within the observed lags)."""
     import numpy as np
     from scipy.optimize import least_squares
     h = np.asarray(h, dtype=np.float64)
     gamma = np.asarray(gamma, dtype=np.float64)
     w = np.sqrt(np.asarray(n, dtype=np.float64))
+    if max_range is None:
+        max_range = 3.0 * float(h.max())
     if init is None:
-        init = (0.1 * gamma[0], max(gamma.max() - 0.1 * gamma[0], 1e-12), max(h.max() / 2.0, 1.0))
+        init = (0.1 * gamma[0], max(gamma.max() - 0.1 * gamma[0], 1e-12), min(max(h.max() / 2.0, 1.0), max_range))
 
     def res(p):
         return w * (gamma / variogram_model(h, model, p[0], p[1], p[2]) - 1.0)
 
-    r = least_squares(res, np.asarray(init, dtype=np.float64), bounds=([0.0, 1e-12, 1e-6], [np.inf, np.inf, np.inf]),
+    r = least_squares(res, np.asarray(init, dtype=np.float64),
+                      bounds=([0.0, 1e-12, 1e-6], [np.inf, np.inf, float(max_range)]),
                       x_scale="jac", xtol=1e-12, ftol=1e-12, gtol=1e-12, max_nfev=2000)
-    return {"theta": (float(r.x[0]), float(r.x[1]), float(r.x[2])), "cost": float(r.cost)}
+    return {"theta": (float(r.x[0]), float(r.x[1]), float(r.x[2])), "cost": float(r.cost),
+            "range_at_bound": bool(r.x[2] >= 0.999 * float(max_range))}
 

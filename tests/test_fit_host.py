@@ -75,3 +75,16 @@ def test_loo_fit_resumes_exactly(tmp_path, monkeypatch):
     assert rest["theta"] == full["theta"]
     assert rest["losses"] == full["losses"][5:]
     assert fit.fit_log_last(path)["step"] == 11
+
+
+def test_wls_range_is_bounded_by_the_observed_lags():
+    """A straight line gamma = c h (no sill within the data) drives an unbounded fit off along the
+    range-sill ridge; the bounded fit stops at three times the longest class and says so."""
+    import numpy as np
+    pytest.importorskip("scipy")
+    from paper_2303_09523_gb300 import fit
+    h = np.arange(1.0, 13.0)
+    gamma = 0.01 * h
+    n = np.full(h.shape, 1000.0)
+    r = fit.fit_variogram_wls(h, gamma, n, "spherical")
+    assert r["theta"][2] <= 3.0 * 12.0 + 1e-9 and r["range_at_bound"]
