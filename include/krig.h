@@ -302,8 +302,8 @@ krig_status krig_empirical_variogram(const krig_volume_desc* desc, const void* d
  *   d_out[8 i + 5..7] = H(G), H(R), H(G, R)
  * Appendix D fixes neither the histogram nor the SSIM constants; here:
  * 256 equal bins over the joint range [min(G,R), max(G,R)] of the pair (a
- * value's bin floor((x - lo) / (hi - lo) * 256) in FP64, clamped to [0, 255];
- * all values in bin 0 when hi = lo), logarithms base 2, population moments
+ * value's bin floor((x - lo) * s), s = 256 / (hi - lo), in FP64, clamped to
+ * [0, 255]; all values in bin 0 when hi = lo), logarithms base 2, population moments
  * over the whole image, c1 = (0.01 L)^2, c2 = (0.03 L)^2, L = max(G) - min(G).
  *   d_G, d_R: device float32 [n_img][H][W].  d_out: device float64 [n_img][8].
  *   d_work: caller-owned device scratch, 256-byte aligned, at least

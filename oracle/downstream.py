@@ -12,7 +12,8 @@ Metrics (Appendix D; readings where the text is silent):
   * RMSE = sqrt(1/(MN) sum (R - G)^2).
   * Histograms for MI and entropy: 256 equal-width bins over the joint value
     range [min(G, R), max(G, R)] of the two images (one binning for both, so
-    that MI(G, G) = H(G)); logarithms base 2 (bits).
+    that MI(G, G) = H(G)), a value's bin floor((x - lo) * 256 / (hi - lo)) with
+    the scale 256 / (hi - lo) formed first; logarithms base 2 (bits).
   * MI = sum p_GR log(p_GR / (p_G p_R)) over the joint histogram.
   * ED = |H(G) - H(R)| / H(G), the relative entropy difference.
   * SSIM: the global formula as printed, with means, variances (the text's
@@ -39,11 +40,13 @@ def rmse(G, R):
 
 
 def _bin_index(X, lo, hi, nbins=NBINS):
-    """Bin of every value in [lo, hi] split into nbins equal bins (the maximum falls in the last)."""
+    """Bin of every value in [lo, hi] split into nbins equal bins (the maximum falls in the last):
+    floor((x - lo) * s) with the bin scale s = nbins / (hi - lo) formed once, in float64."""
     X = np.asarray(X, dtype=np.float64)
     if hi <= lo:
         return np.zeros(X.shape, dtype=np.int64)
-    b = np.floor((X - lo) / (hi - lo) * nbins).astype(np.int64)
+    scale = float(nbins) / (float(hi) - float(lo))
+    b = np.floor((X - lo) * scale).astype(np.int64)
     return np.clip(b, 0, nbins - 1)
 
 

@@ -8,8 +8,9 @@
 // pair, one binning for both images, logarithms base 2; MI(G, G) uses G's own
 // range; ED = |H(G) - H(R)| / H(G) on the joint binning; SSIM is the printed
 // global formula with population moments, c1 = (0.01 L)^2, c2 = (0.03 L)^2 and
-// L = max(G) - min(G).  A value's bin is floor((x - lo) / (hi - lo) * 256) in
-// FP64, clamped to [0, 255] (all zero when hi <= lo).
+// L = max(G) - min(G).  A value's bin is floor((x - lo) * s) with s = 256 /
+// (hi - lo) formed once per image, in FP64, clamped to [0, 255] (all zero when
+// hi <= lo); one FP64 division per image instead of one per value.
 //
 // Four launches per call: per-block partial sums and extrema, per-image
 // means and ranges (and the histograms zeroed), the histograms (joint
@@ -151,11 +152,16 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_stats(int nb, int64_t npix,
     if (threadIdx.x < SIM_BINS) w.own[(size_t)img * SIM_BINS + threadIdx.x] = 0u;
 }
 
-__device__ __forceinline__ int sim_bin(double x, double lo, double hi)
+// Bin of x: floor((x - lo) * scale), scale = 256 / (hi - lo) formed once per image
+// (0 when hi <= lo: every value in bin 0).  FP64, the oracle's arithmetic.
+__device__ __forceinline__ int sim_bin(double x, double lo, double scale)
 {
-    if (!(hi > lo)) return 0;
-    const double b = floor((x - lo) / (hi - lo) * (double)SIM_BINS);
+    const double b = floor((x - lo) * scale);
     return b < 0.0 ? 0 : (b > SIM_BINS - 1 ? SIM_BINS - 1 : (int)b);
+}
+__device__ __forceinline__ double sim_scale(double lo, double hi)
+{
+    return hi > lo ? (double)SIM_BINS / (hi - lo) : 0.0;
 }
 
 // The histograms, and the centred sums sum (G - mx)^2, (R - my)^2, (G - mx)(R - my)
@@ -166,7 +172,8 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_hist(const float* G, const 
     __shared__ double red[SIM_THREADS / 32];
     const int img = blockIdx.y, nb = gridDim.x;
     const double* st = w.stats + (size_t)img * SIM_STATS;
-    const double lo = st[6], hi = st[7], glo = st[8], ghi = st[9];
+    const double lo = st[6], glo = st[8];
+    const double sc = sim_scale(st[6], st[7]), gsc = sim_scale(st[8], st[9]);
     for (int e = threadIdx.x; e < SIM_BINS; e += SIM_THREADS) own[e] = 0u;
     __syncthreads();
     const float* g = G + (size_t)img * npix;
@@ -176,8 +183,8 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_hist(const float* G, const 
     double c[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)SIM_THREADS + threadIdx.x; i < npix; i += (int64_t)nb * SIM_THREADS) {
         const double a = g[i], b = r[i];
-        atomicAdd(&joint[sim_bin(a, lo, hi) * SIM_BINS + sim_bin(b, lo, hi)], 1u);
-        atomicAdd(&own[sim_bin(a, glo, ghi)], 1u);
+        atomicAdd(&joint[sim_bin(a, lo, sc) * SIM_BINS + sim_bin(b, lo, sc)], 1u);
+        atomicAdd(&own[sim_bin(a, glo, gsc)], 1u);
         c[0] += (a - mx) * (a - mx);
         c[1] += (b - my) * (b - my);
         c[2] += (a - mx) * (b - my);
