@@ -516,6 +516,9 @@ def main():
     ap.add_argument("--no-downstream", action="store_true",
                     help="skip universal kriging, marching cubes and the similarity metrics")
     ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
+    ap.add_argument("--section", default=None, choices=["uk", "mc", "sim", "loo", "variogram"],
+                    help="run only one of the lines beside the headline and print it (a profiling mode; "
+                         "not the benchmark's result line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -540,6 +543,12 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     extra = {}
+    if args.section:
+        fn = {"uk": time_uk, "mc": time_mc, "sim": similarity_table,
+              "loo": lambda a, d, s_, f, with_oracle: time_loo(a, d, s_, f, None, with_oracle=with_oracle),
+              "variogram": lambda a, d, s_, f, with_oracle: time_variogram(a, d, s_, f)}[args.section]
+        print(json.dumps({"section": args.section, "result": fn(args, dev, stream, flush, with_oracle=not args.no_cpu)}))
+        return
     lead = rank == 0 and world == 1
 
     # the spine configuration's variogram is fitted to its slices: gradient descent on the

@@ -129,7 +129,19 @@ struct McArgs {
     float* tri;          // [max_tri][9]
     int64_t max_tri;
     int64_t* ntri;       // device, total
+    uint64_t mcw, mch;   // krig_udiv multipliers: by W - 1, by H - 1
 };
+
+// Cube index -> (x, y, z), multiply-high divisions (cube < 2^32).
+__device__ __forceinline__ void mc_xyz(const McArgs& a, int64_t cube, int& x, int& y, int& z)
+{
+    const uint32_t c = (uint32_t)cube;
+    const uint32_t r = krig_udiv(c, a.mcw);
+    x = (int)(c - r * (uint32_t)(a.W - 1));
+    const uint32_t zz = krig_udiv(r, a.mch);
+    y = (int)(r - zz * (uint32_t)(a.H - 1));
+    z = (int)zz;
+}
 
 // Corner `end` (0: lower index, 1: upper) of edge e, the same list as kEdge:
 // edges 0-3 run along x, 4-7 along y, 8-11 along z.
@@ -152,10 +164,8 @@ __device__ __forceinline__ int kEdgeDev(int e, int end)
 
 __device__ __forceinline__ int mc_case(const McArgs& a, int64_t cube)
 {
-    const int cw = a.W - 1, ch = a.H - 1;
-    const int x = (int)(cube % cw);
-    const int64_t r = cube / cw;
-    const int y = (int)(r % ch), z = (int)(r / ch);
+    int x, y, z;
+    mc_xyz(a, cube, x, y, z);
     const size_t plane = (size_t)a.H * a.W;
     const float* p = a.vol + (size_t)z * plane + (size_t)y * a.W + x;
     int c = 0;
@@ -242,15 +252,13 @@ __global__ void __launch_bounds__(MC_THREADS) k_mc_emit(const McArgs a, const __
     int woff = 0;
     for (int w = 0; w < warp; ++w) woff += wsum[w];
     int64_t out = a.bsum[blockIdx.x] + woff + incl - cnt;
-    const int cw = a.W - 1, ch = a.H - 1;
     const size_t plane = (size_t)a.H * a.W;
     for (int k = 0; k < MC_PER_THREAD; ++k) {
         const int c = cs[k];
         if (!T.ntri[c]) continue;
         const int64_t cube = base + (int64_t)threadIdx.x * MC_PER_THREAD + k;
-        const int x = (int)(cube % cw);
-        const int64_t r = cube / cw;
-        const int y = (int)(r % ch), z = (int)(r / ch);
+        int x, y, z;
+        mc_xyz(a, cube, x, y, z);
         const float* p = a.vol + (size_t)z * plane + (size_t)y * a.W + x;
         float v[8];
         v[0] = p[0];
@@ -316,7 +324,7 @@ extern "C" krig_status krig_marching_cubes(const float* d_vol, int32_t D, int32_
     if (work_bytes < need)
         return mc_fail(KRIG_EWORKSPACE, "workspace too small: " + std::to_string(work_bytes) + " bytes, need " +
                                             std::to_string(need));
-    if (nb > (int64_t)INT32_MAX) return mc_fail(KRIG_EINVAL, "volume too large");
+    if (ncubes >= (1LL << 32)) return mc_fail(KRIG_EINVAL, "volume too large: at most 2^32 - 1 cubes");
     McArgs a;
     a.vol = d_vol;
     a.D = D;
@@ -329,6 +337,8 @@ extern "C" krig_status krig_marching_cubes(const float* d_vol, int32_t D, int32_
     a.tri = d_tri;
     a.max_tri = max_tri;
     a.ntri = d_ntri;
+    a.mcw = krig_udiv_magic((uint32_t)(W - 1));
+    a.mch = krig_udiv_magic((uint32_t)(H - 1));
     const McTable& T = table();
     cudaStream_t st = (cudaStream_t)stream;
     k_mc_classify<<<(unsigned)nb, MC_THREADS, 0, st>>>(a, T);

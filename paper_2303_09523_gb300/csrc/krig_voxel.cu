@@ -311,6 +311,175 @@ __global__ void __launch_bounds__(LWARPS * 32, 1) k_voxel_lane(const __grid_cons
 #undef BV
 }
 
+// ---------------------------------------------------------------------------
+// PMX for windows of up to 18 points: one voxel per lane, as k_voxel_lane, but
+// the factorisation and the sweeps in FP32 and one step of FP64 iterative
+// refinement: x0 = C^-1 b in FP32, the residual b - C x0 in FP64 (C and b
+// from the FP64 lag tables), the correction by the FP32 factors, x = x0 + d
+// in FP64; then phi, w, the estimate and the variance in FP64.  The FP64 work
+// per voxel is the residual (2 K^2 FMAs) and the combine, against the K^3/6 +
+// 2 K^2 of the plain FP64 form.
+// ---------------------------------------------------------------------------
+constexpr int MWARPS = 6;
+constexpr size_t MSMEM = (size_t)MWARPS * 32 * (LT * sizeof(float) + 2 * LK * sizeof(double) + 2 * LK * sizeof(float));
+
+__global__ void __launch_bounds__(MWARPS * 32, 1) k_voxel_lane_mx(const __grid_constant__ KrigLaunch P)
+{
+    extern __shared__ __align__(16) unsigned char msm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = msm + (size_t)warp * 32 * (LT * sizeof(float) + 2 * LK * sizeof(double) + 2 * LK * sizeof(float));
+    float* const Lm = (float*)base;                       // [LT][32] factor
+    double* const xu = (double*)(Lm + LT * 32);           // [LK][32] solutions (FP64)
+    double* const xv = xu + LK * 32;
+    float* const ru = (float*)(xv + LK * 32);             // [LK][32] sweep vectors (FP32)
+    float* const rv = ru + LK * 32;
+#define LE(e) Lm[(e) * 32 + lane]
+#define XU(i) xu[(i) * 32 + lane]
+#define XV(i) xv[(i) * 32 + lane]
+#define RU(i) ru[(i) * 32 + lane]
+#define RV(i) rv[(i) * 32 + lane]
+    const int64_t stride = (int64_t)gridDim.x * MWARPS * 32;
+    for (int64_t vox = ((int64_t)blockIdx.x * MWARPS + warp) * 32 + lane; vox < P.n_vox; vox += stride) {
+        const int v = krig_find_vol(P, vox, 2);
+        const KrigVol& V = P.vol[v];
+        const int r = V.r;
+        if (r > 1) continue;  // voxel of the warp-per-voxel kernel
+        const int64_t local = vox - V.vox_begin;
+        const int64_t plane = (int64_t)V.H * V.W;
+        const int z = (int)(local / plane);
+        const int64_t pix = local % plane;
+        const int y = (int)(pix / V.W), x = (int)(pix % V.W);
+        const int g = V.g, j = z / g, t = z % g;
+        const bool f64 = V.dtype == KRIG_F64;
+        if (t == 0) {  // known slice: copy through
+            const double val = in_value(P.in[v], V.dtype, V.scale, (int64_t)j * plane + pix);
+            if (f64) ((double*)P.out[v])[local] = val;
+            else ((float*)P.out[v])[local] = (float)val;
+            if (P.var[v]) P.var[v][local] = 0.0f;
+            continue;
+        }
+        LagDims d{r, g, 2 * r + 1, r + 1};
+        const double* gC = (const double*)(P.ws + V.lag_off);
+        const double* g0 = gC + d.nC();
+        const int lx = min(x, r), rx = min(V.W - 1 - x, r), ly = min(y, r), ry = min(V.H - 1 - y, r);
+        const int nx = lx + rx + 1, ny = ly + ry + 1, nxy = nx * ny;
+        const int K = 2 * nxy;
+        // FP32 system (lower triangle) and right-hand sides
+        for (int i = 0; i < K; ++i) {
+            const int si = i / nxy, dyi = (i / nx) % ny - ly, dxi = i % nx - lx;
+            for (int k = 0; k <= i; ++k) {
+                const int sk = k / nxy, dyk = (k / nx) % ny - ly, dxk = k % nx - lx;
+                LE(i * (i + 1) / 2 + k) = (float)__ldg(gC + d.iC(si != sk, abs(dyi - dyk), abs(dxi - dxk)));
+            }
+            RU(i) = (float)__ldg(g0 + d.i0(t, si, abs(dyi), abs(dxi)));
+            RV(i) = 1.0f;
+        }
+        // FP32 LDL'
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            const int kk = k * (k + 1) / 2;
+            const float dk = LE(kk + k);
+            if (!(dk > 0.0f)) {
+                ok = false;
+                break;
+            }
+            const float inv = 1.0f / dk;
+            LE(kk + k) = inv;
+            for (int i = k + 1; i < K; ++i) {
+                const int ii = i * (i + 1) / 2;
+                const float ti = LE(ii + k);
+                const float li = ti * inv;
+                LE(ii + k) = li;
+#pragma unroll 4
+                for (int jj = k + 1; jj < i; ++jj) LE(ii + jj) = fmaf(-ti, LE(jj * (jj + 1) / 2 + k), LE(ii + jj));
+                LE(ii + i) = fmaf(-ti, li, LE(ii + i));
+            }
+        }
+        double est, var;
+        if (ok) {
+            // x = C^-1 b with the FP32 factors, applied to (RU, RV) in place
+            auto sweep = [&]() {
+                for (int i = 1; i < K; ++i) {
+                    const int ii = i * (i + 1) / 2;
+                    float au = RU(i), av = RV(i);
+#pragma unroll 4
+                    for (int k = 0; k < i; ++k) {
+                        const float l = LE(ii + k);
+                        au = fmaf(-l, RU(k), au);
+                        av = fmaf(-l, RV(k), av);
+                    }
+                    RU(i) = au;
+                    RV(i) = av;
+                }
+                for (int i = 0; i < K; ++i) {
+                    const float inv = LE(i * (i + 1) / 2 + i);
+                    RU(i) *= inv;
+                    RV(i) *= inv;
+                }
+                for (int i = K - 2; i >= 0; --i) {
+                    float au = RU(i), av = RV(i);
+#pragma unroll 4
+                    for (int k = i + 1; k < K; ++k) {
+                        const float l = LE(k * (k + 1) / 2 + i);
+                        au = fmaf(-l, RU(k), au);
+                        av = fmaf(-l, RV(k), av);
+                    }
+                    RU(i) = au;
+                    RV(i) = av;
+                }
+            };
+            sweep();
+            for (int i = 0; i < K; ++i) {
+                XU(i) = (double)RU(i);
+                XV(i) = (double)RV(i);
+            }
+            // one FP64 refinement step: residual b - C x in FP64, corrected by the FP32 factors
+            for (int i = 0; i < K; ++i) {
+                const int si = i / nxy, dyi = (i / nx) % ny - ly, dxi = i % nx - lx;
+                double au = __ldg(g0 + d.i0(t, si, abs(dyi), abs(dxi))), av = 1.0;
+                for (int k = 0; k < K; ++k) {
+                    const int sk = k / nxy, dyk = (k / nx) % ny - ly, dxk = k % nx - lx;
+                    const double c = __ldg(gC + d.iC(si != sk, abs(dyi - dyk), abs(dxi - dxk)));
+                    au = fma(-c, XU(k), au);
+                    av = fma(-c, XV(k), av);
+                }
+                RU(i) = (float)au;
+                RV(i) = (float)av;
+            }
+            sweep();
+            double su = 0.0, sv = 0.0;
+            for (int i = 0; i < K; ++i) {
+                XU(i) += (double)RU(i);
+                XV(i) += (double)RV(i);
+                su += XU(i);
+                sv += XV(i);
+            }
+            const double phi = (su - 1.0) / sv;
+            double wz = 0.0, wc = 0.0;
+            for (int i = 0; i < K; ++i) {
+                const int si = i / nxy, dyi = (i / nx) % ny - ly, dxi = i % nx - lx;
+                const double w = XU(i) - phi * XV(i);
+                const int64_t idx = (int64_t)(j + si) * plane + (int64_t)(y + dyi) * V.W + (x + dxi);
+                wz += w * in_value(P.in[v], V.dtype, V.scale, idx);
+                wc += w * __ldg(g0 + d.i0(t, si, abs(dyi), abs(dxi)));
+            }
+            est = wz;
+            var = gC[0] - wc - phi;
+        } else {
+            est = var = __longlong_as_double(0x7ff8000000000000LL);
+            krig_set_status(P.status, KRIG_DEV_SINGULAR);
+        }
+        if (f64) ((double*)P.out[v])[local] = est;
+        else ((float*)P.out[v])[local] = (float)est;
+        if (P.var[v]) P.var[v][local] = (float)var;
+    }
+#undef LE
+#undef XU
+#undef XV
+#undef RU
+#undef RV
+}
+
 template <typename TF, int RMAX>
 static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st, int rmin)
 {
@@ -331,16 +500,20 @@ static int launch_voxel_t(const KrigLaunch& L, cudaStream_t st, int rmin)
     return (int)cudaGetLastError();
 }
 
-static int launch_voxel_lane(const KrigLaunch& L, cudaStream_t st)
+static int launch_voxel_lane(const KrigLaunch& L, cudaStream_t st, bool mixed)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_voxel_lane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LSMEM);
+    const int warps = mixed ? MWARPS : LWARPS;
+    const size_t smem = mixed ? MSMEM : LSMEM;
+    cudaError_t e = mixed ? cudaFuncSetAttribute(k_voxel_lane_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(k_voxel_lane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     const int sms = krig_device_sm_count();
     int64_t grid = sms > 0 ? sms : 1;
-    const int64_t need = (L.n_vox + LWARPS * 32 - 1) / (LWARPS * 32);
+    const int64_t need = (L.n_vox + warps * 32 - 1) / (warps * 32);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_voxel_lane<<<(unsigned)grid, LWARPS * 32, LSMEM, st>>>(L);
+    if (mixed) k_voxel_lane_mx<<<(unsigned)grid, warps * 32, smem, st>>>(L);
+    else k_voxel_lane<<<(unsigned)grid, warps * 32, smem, st>>>(L);
     return (int)cudaGetLastError();
 }
 
@@ -354,17 +527,13 @@ int krig_launch_voxel(const KrigLaunch& L, int form, void* stream)
     int rmax = 0;
     for (int v = 0; v < L.n_vols; ++v) rmax = L.vol[v].r > rmax ? L.vol[v].r : rmax;
     const bool fp64 = form == KRIG_FORM_P64;
-    if (fp64) {
-        // voxels of volumes with r <= 1: one per lane; r = 2: one per warp
-        int rmin = 0;
-        for (int v = 0; v < L.n_vols; ++v) rmin = (v == 0 || L.vol[v].r < rmin) ? L.vol[v].r : rmin;
-        if (rmin <= 1) {
-            const int rc = launch_voxel_lane(L, st);
-            if (rc) return rc;
-        }
-        return rmax == 2 ? launch_voxel_t<double, 2>(L, st, 2) : 0;
+    // voxels of volumes with r <= 1: one per lane; r = 2: one per warp
+    int rmin = 0;
+    for (int v = 0; v < L.n_vols; ++v) rmin = (v == 0 || L.vol[v].r < rmin) ? L.vol[v].r : rmin;
+    if (rmin <= 1) {
+        const int rc = launch_voxel_lane(L, st, !fp64);
+        if (rc) return rc;
     }
-    if (rmax == 0) return launch_voxel_t<float, 0>(L, st, 0);
-    if (rmax == 1) return launch_voxel_t<float, 1>(L, st, 0);
-    return launch_voxel_t<float, 2>(L, st, 0);
+    if (rmax < 2) return 0;
+    return fp64 ? launch_voxel_t<double, 2>(L, st, 2) : launch_voxel_t<float, 2>(L, st, 2);
 }
