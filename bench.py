@@ -241,7 +241,7 @@ def err_vs_oracle(outs, variances, sample):
 class DsHarness:
     """Device buffers, plan (autotuned for batches) and the captured CUDA graph of one workload."""
 
-    def __init__(self, vols, dev, stream, autotune):
+    def __init__(self, vols, dev, stream, autotune, schedule=None):
         import torch
         from paper_2303_09523_gb300 import binding
         self.vols = vols
@@ -256,7 +256,12 @@ class DsHarness:
                      for v, c in zip(vols, codes)]
         self.params = binding.variogram_tensor([v.variogram() for v in vols], device=dev)
         self.plan = binding.Plan(self.descs, form="DS", device=dev)
-        self.chunk = self.plan.autotune(self.ts, self.outs, self.params, iters=3, stream=stream) if autotune else None
+        self.chunk = None
+        if schedule is not None:
+            self.plan.set_schedule(*schedule)
+            self.chunk = schedule[0]
+        elif autotune:
+            self.chunk = self.plan.autotune(self.ts, self.outs, self.params, iters=3, stream=stream)
         self.graph = self.plan.capture(self.ts, self.outs, self.params)
         self.n_missing = sum(v.n_missing for v in vols)
         self.abytes = sum(algorithmic_bytes(v) for v in vols)
@@ -406,7 +411,7 @@ def measure_workload(wl_key, vols, wl_name, args, dev, stream, flush, world, dis
     clock pass, e2e, error against the FP64 oracle on a seeded sample, the oracle's CPU rate."""
     import torch
     steps = args.steps if steps is None else steps
-    h = DsHarness(vols, dev, stream, autotune=len(vols) > 1)
+    h = DsHarness(vols, dev, stream, autotune=len(vols) > 1, schedule=getattr(args, "schedule_tuple", None))
     for _ in range(args.warmup):
         h.replay()
     h.plan.device_status(stream)
@@ -423,7 +428,7 @@ def measure_workload(wl_key, vols, wl_name, args, dev, stream, flush, world, dis
            "ms_per_step": total_ms / steps, "interpolated_voxels_per_step": h.n_missing,
            "volumes": len(vols), "workload": wl_name}
     if h.chunk is not None:
-        res["autotuned_gaps_per_item"] = h.chunk
+        res["autotuned_gaps_per_item"], res["autotuned_stencil_blocks_per_sm"] = h.plan.schedule()
     solve_ms, apply_ms = h.kernel_ms(min(max(steps, 20), 200), flush)
     res["roofline"] = roofline_of(h, apply_ms, solve_ms, wl_key)
     if clk is not None:
@@ -516,10 +521,13 @@ def main():
     ap.add_argument("--no-downstream", action="store_true",
                     help="skip universal kriging, marching cubes and the similarity metrics")
     ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
+    ap.add_argument("--schedule", default=None,
+                    help="CHUNK,BLOCKS_PER_SM: set the DS schedule instead of autotuning (profiling one fixed launch)")
     ap.add_argument("--section", default=None, choices=["uk", "mc", "sim", "loo", "variogram"],
                     help="run only one of the lines beside the headline and print it (a profiling mode; "
                          "not the benchmark's result line)")
     args = ap.parse_args()
+    args.schedule_tuple = tuple(int(x) for x in args.schedule.split(",")) if args.schedule else None
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
 
@@ -631,7 +639,7 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
-        for k in ("autotuned_gaps_per_item", "interpolated_voxels_per_step"):
+        for k in ("autotuned_gaps_per_item", "autotuned_stencil_blocks_per_sm", "interpolated_voxels_per_step"):
             if k in head:
                 line["config"][k] = head[k]
         line.update(extra)

@@ -204,13 +204,27 @@ krig_status krig_backward(krig_plan_t plan, const void* const* d_slices, const k
 
 /* Autotune the DS schedule on the caller's data: time krig_interpolate (iters
  * calls each, synchronously on `stream`) for several work-item lengths (gaps
- * per item: 1, 2, 3, 4, 6, 8, 12, 16 and whole sub-blocks) and keep the
- * fastest.  The choice changes only the schedule: every choice gives
+ * per item: 1, 2, 3, 4, 6, 8, 12, 16 and whole sub-blocks), each with the
+ * stencil launched at as many blocks per SM as fit or at one, and keep the
+ * fastest pair.  The choice changes only the schedule: every choice gives
  * bit-identical results.  Writes to d_out.  Not capturable; call it before
- * capturing a graph.  *chunk_out (nullable) receives the chosen length.
+ * capturing a graph.  *chunk_out (nullable) receives the chosen length
+ * (krig_plan_schedule reports both choices).
  * Errors: as krig_interpolate; KRIG_EUNSUPPORTED for P64 / PMX plans. */
 krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, void* const* d_out,
                                const krig_variogram* d_params, int32_t iters, void* stream, int32_t* chunk_out);
+
+/* The plan's DS schedule: gaps per work item (of volume 0; every volume uses the
+ * same length, capped at its sub-block) and stencil blocks per SM (0: as many as
+ * fit).  Either pointer nullable.  Errors: KRIG_EINVAL. */
+krig_status krig_plan_schedule(krig_plan_t plan, int32_t* chunk_out, int32_t* blocks_per_sm_out);
+
+/* Set the DS schedule directly (a result of krig_plan_autotune kept from an
+ * earlier run): gaps per work item (>= 1; capped at each volume's sub-block)
+ * and stencil blocks per SM (0: as many as fit).  Results are bit-identical for
+ * every schedule.  Host only; call it before capturing a graph.
+ * Errors: KRIG_EINVAL, KRIG_EUNSUPPORTED (P64 / PMX plans). */
+krig_status krig_plan_set_schedule(krig_plan_t plan, int32_t chunk, int32_t blocks_per_sm);
 
 /* Wait for the stream, then return and clear the plan's device error bits:
  * KRIG_OK, KRIG_ESINGULAR or KRIG_ETIMEOUT (the first set, in that order). */
@@ -225,6 +239,20 @@ krig_status krig_plan_device_status(krig_plan_t plan, void* stream);
 #define KRIG_TIMING_KINDS 4
 krig_status krig_plan_set_timing(krig_plan_t plan, int32_t enable);
 krig_status krig_plan_get_timing(krig_plan_t plan, double* ms_out, int64_t* launches_out);
+
+/* Kriging variance as a class table (the variance of a missing voxel depends only
+ * on its geometry class, like its weights): after krig_interpolate on a DS plan
+ * without drift flags, the variance of voxel (x, y, j*g + t), 1 <= t < g, of
+ * volume v is
+ *     h_table[(h_cy[y] * ncx + h_cx[x]) * 8 + t - 1]
+ * (0 at known slices) -- the same values krig_interpolate writes into d_var,
+ * without the variance volume.  Fills (each nullable): h_table host float
+ * [ncy][ncx][8] (waits for `stream`, then copies), h_cx host int32 [W], h_cy
+ * host int32 [H] (class of each coordinate), *ncx_out, *ncy_out.
+ * Errors: KRIG_EINVAL, KRIG_EUNSUPPORTED (P64 / PMX / drift plans),
+ * KRIG_EWORKSPACE, KRIG_ECUDA. */
+krig_status krig_plan_variance_table(krig_plan_t plan, int32_t v, float* h_table, int32_t* h_cx, int32_t* h_cy,
+                                     int32_t* ncx_out, int32_t* ncy_out, void* stream);
 
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char* krig_last_error(void);

@@ -108,6 +108,14 @@ def lib(build_if_missing: bool = False):
     L.krig_marching_cubes.restype = ctypes.c_int
     L.krig_marching_cubes_table.argtypes = [ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_uint8)]
     L.krig_marching_cubes_table.restype = None
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.krig_plan_schedule.argtypes = [vp, i32p, i32p]
+    L.krig_plan_schedule.restype = ctypes.c_int
+    L.krig_plan_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    L.krig_plan_set_schedule.restype = ctypes.c_int
+    L.krig_plan_variance_table.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), i32p, i32p, i32p, i32p,
+                                           vp]
+    L.krig_plan_variance_table.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -230,6 +238,34 @@ class Plan:
             self.interpolate(slices, outs, params, variances, s)
         torch.cuda.current_stream().wait_stream(s)
         return g
+
+    def schedule(self):
+        """(gaps per work item, stencil blocks per SM; 0 = as many as fit): krig_plan_schedule."""
+        c, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.krig_plan_schedule(self.handle, ctypes.byref(c), ctypes.byref(b)))
+        return c.value, b.value
+
+    def set_schedule(self, chunk, blocks_per_sm=0):
+        """Set the DS schedule (krig_plan_set_schedule), e.g. a kept autotune result."""
+        _check(self._lib.krig_plan_set_schedule(self.handle, int(chunk), int(blocks_per_sm)))
+
+    def variance_table(self, v=0, stream=None):
+        """Volume v's kriging variance by geometry class (krig_plan_variance_table): returns
+        (table [ncy, ncx, 8] float32, cx [W] int32, cy [H] int32); the variance of (x, y, j g + t)
+        is table[cy[y], cx[x], t - 1]."""
+        import numpy as np
+        d = self.descs[v]
+        ncx, ncy = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.krig_plan_variance_table(self.handle, v, None, None, None, ctypes.byref(ncx), ctypes.byref(ncy),
+                                                  _stream(stream)))
+        table = np.zeros((ncy.value, ncx.value, 8), dtype=np.float32)
+        cx = np.zeros(int(d["W"]), dtype=np.int32)
+        cy = np.zeros(int(d["H"]), dtype=np.int32)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        _check(self._lib.krig_plan_variance_table(self.handle, v, table.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  cx.ctypes.data_as(i32p), cy.ctypes.data_as(i32p), None, None,
+                                                  _stream(stream)))
+        return table, cx, cy
 
     def device_status(self, stream=None):
         _check(self._lib.krig_plan_device_status(self.handle, _stream(stream)))

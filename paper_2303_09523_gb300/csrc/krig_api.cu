@@ -371,7 +371,7 @@ krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, vo
         return fail(KRIG_ECUDA, "cudaEventCreate failed");
     const int saved_timing = plan->timing;
     plan->timing = 0;
-    int best = plan->L.vol[0].chunk, last = -1;
+    int best = plan->L.vol[0].chunk, best_bps = plan->L.ds_blocks_per_sm, last = -1;
     float best_ms = 1e30f;
     krig_status s = KRIG_OK;
     for (int c : cand) {
@@ -379,29 +379,55 @@ krig_status krig_plan_autotune(krig_plan_t plan, const void* const* d_slices, vo
         if (eff == last) continue;
         last = eff;
         set_chunk(plan, eff);
-        s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);  // warm-up
-        if (s != KRIG_OK) break;
-        cudaEventRecord(a, st);
-        for (int i = 0; i < iters && s == KRIG_OK; ++i) s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);
-        cudaEventRecord(b, st);
-        if (s != KRIG_OK) break;
-        if (cudaEventSynchronize(b) != cudaSuccess) {
-            s = fail(KRIG_ECUDA, "autotune timing failed");
-            break;
+        // launch shape: as many stencil blocks per SM as fit, or one
+        for (int bps = 0; bps <= 1 && s == KRIG_OK; ++bps) {
+            plan->L.ds_blocks_per_sm = bps;
+            s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);  // warm-up
+            if (s != KRIG_OK) break;
+            cudaEventRecord(a, st);
+            for (int i = 0; i < iters && s == KRIG_OK; ++i)
+                s = krig_interpolate(plan, d_slices, d_out, nullptr, d_params, stream);
+            cudaEventRecord(b, st);
+            if (s != KRIG_OK) break;
+            if (cudaEventSynchronize(b) != cudaSuccess) {
+                s = fail(KRIG_ECUDA, "autotune timing failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = eff;
+                best_bps = bps;
+            }
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = eff;
-        }
+        if (s != KRIG_OK) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     plan->timing = saved_timing;
     set_chunk(plan, best);
+    plan->L.ds_blocks_per_sm = best_bps;
     if (chunk_out) *chunk_out = best;
     return s;
+}
+
+krig_status krig_plan_set_schedule(krig_plan_t plan, int32_t chunk, int32_t blocks_per_sm)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (plan->form != KRIG_FORM_DS) return fail(KRIG_EUNSUPPORTED, "the schedule applies to the DS form");
+    if (chunk < 1 || blocks_per_sm < 0) return fail(KRIG_EINVAL, "chunk must be >= 1 and blocks_per_sm >= 0");
+    set_chunk(plan, chunk);
+    plan->L.ds_blocks_per_sm = blocks_per_sm;
+    return KRIG_OK;
+}
+
+krig_status krig_plan_schedule(krig_plan_t plan, int32_t* chunk_out, int32_t* blocks_per_sm_out)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (chunk_out) *chunk_out = plan->L.vol[0].chunk;
+    if (blocks_per_sm_out) *blocks_per_sm_out = plan->L.ds_blocks_per_sm;
+    return KRIG_OK;
 }
 
 krig_status krig_plan_device_status(krig_plan_t plan, void* stream)
@@ -451,6 +477,38 @@ krig_status krig_plan_get_timing(krig_plan_t plan, double* ms_out, int64_t* laun
         if (launches_out) launches_out[k] = plan->launches[k];
         plan->ms[k] = 0;
         plan->launches[k] = 0;
+    }
+    return KRIG_OK;
+}
+
+krig_status krig_plan_variance_table(krig_plan_t plan, int32_t v, float* h_table, int32_t* h_cx, int32_t* h_cy,
+                                     int32_t* ncx_out, int32_t* ncy_out, void* stream)
+{
+    if (!plan) return fail(KRIG_EINVAL, "plan is NULL");
+    if (plan->form != KRIG_FORM_DS || plan->L.uk_slabs)
+        return fail(KRIG_EUNSUPPORTED, "the variance class table belongs to DS plans without drift flags");
+    if (!plan->ws) return fail(KRIG_EWORKSPACE, "no workspace set");
+    if (v < 0 || v >= plan->L.n_vols) return fail(KRIG_EINVAL, "volume index %d out of range", v);
+    const KrigVol& V = plan->L.vol[v];
+    if (ncx_out) *ncx_out = V.ncx;
+    if (ncy_out) *ncy_out = V.ncy;
+    // class of each coordinate: the truncation slot of its window, mapped to the compact class
+    if (h_cx)
+        for (int x = 0; x < V.W; ++x) {
+            const int l = x < V.r ? x : V.r, rr = (V.W - 1 - x) < V.r ? (V.W - 1 - x) : V.r;
+            h_cx[x] = V.xmap[l * (V.r + 1) + rr];
+        }
+    if (h_cy)
+        for (int y = 0; y < V.H; ++y) {
+            const int l = y < V.r ? y : V.r, rr = (V.H - 1 - y) < V.r ? (V.H - 1 - y) : V.r;
+            h_cy[y] = V.ymap[l * (V.r + 1) + rr];
+        }
+    if (h_table) {
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = cudaMemcpyAsync(h_table, plan->ws + V.vtab_off, (size_t)krig_vtab_bytes(V),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the variance table");
     }
     return KRIG_OK;
 }

@@ -1134,6 +1134,7 @@ int krig_launch_ds_apply_t(const KrigLaunch& L, const DsTma& T, cudaStream_t st)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ds_apply<TI>, DS_BLOCK, smem);
     if (e != cudaSuccess) return (int)e;
     const int sms = krig_device_sm_count();
+    if (L.ds_blocks_per_sm > 0 && L.ds_blocks_per_sm < per_sm) per_sm = L.ds_blocks_per_sm;
     int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     if (grid > L.n_items) grid = L.n_items;
     if (grid < 1) grid = 1;

@@ -111,6 +111,7 @@ struct KrigLaunch {
     int32_t fault_timeout;      // test only: make one bounded device wait give up
     int32_t accumulate;         // LOO backward: add into grad_slices / grad_params
     int64_t n_loo_classes, n_loo_items, n_loo_adj;
+    int32_t ds_blocks_per_sm;   // stencil blocks per SM (0: as many as fit; set by the autotuner)
     int32_t clamp;              // clamp DS estimates to their sub-block's known range
     int64_t n_mm_blocks;        // sub-blocks over all volumes (clamp plans)
     int32_t uk_drift;           // universal kriging drift: 0 {1}, 1 {1, z}, 2 {1, x, y, z}

@@ -64,12 +64,16 @@ def test_autotune_keeps_results_bit_identical(mix):
     ref = [o.clone() for o in outs]
     chunk = plan.autotune(ts, outs, params, iters=2)
     assert chunk >= 1
-    for o in outs:
-        o.zero_()
-    plan.interpolate(ts, outs, params)
-    plan.device_status()
-    for a, b in zip(outs, ref):
-        assert torch.equal(a, b)
+    c2, bps = plan.schedule()
+    assert c2 == min(chunk, max((v.n - 1 + v.n_sub_blocks - 1) // v.n_sub_blocks for v in sub[:1])) and bps in (0, 1)
+    for sched in ((chunk, bps), (1, 1), (3, 0)):  # the tuned one, then fixed schedules and launch shapes
+        plan.set_schedule(*sched)
+        for o in outs:
+            o.zero_()
+        plan.interpolate(ts, outs, params)
+        plan.device_status()
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
     plan.close()
 
 
@@ -96,4 +100,29 @@ def test_graph_replay_matches_eager_and_follows_new_parameters(mix):
     plan.device_status()
     for a, b in zip(outs, eager):
         assert torch.equal(a, b)
+    plan.close()
+
+
+def test_variance_class_table_reproduces_the_variance_volume():
+    """krig_plan_variance_table: the variance volume rebuilt from the class table and the class
+    maps equals, bit for bit, the one krig_interpolate writes (both volumes of a two-volume plan)."""
+    vols = [phantoms.random_stack(5, 37, 45, 3, 2, k=2, seed=91, model="exponential"),
+            phantoms.random_stack(4, 20, 64, 5, 1, k=1, seed=92)]
+    ts = [torch.from_numpy(np.ascontiguousarray(v.slices)).cuda() for v in vols]
+    descs = [binding.desc_for(tuple(t.shape), v.zfactor, v.half_w, v.n_sub_blocks, binding.F32)
+             for v, t in zip(vols, ts)]
+    plan = binding.Plan(descs, form="DS")
+    outs = [torch.empty((v.n_out, v.H, v.W), dtype=torch.float32, device="cuda") for v in vols]
+    var = [torch.empty_like(o) for o in outs]
+    params = binding.variogram_tensor([v.variogram() for v in vols])
+    plan.interpolate(ts, outs, params, var)
+    plan.device_status()
+    for i, v in enumerate(vols):
+        table, cx, cy = plan.variance_table(i)
+        rebuilt = np.zeros((v.n_out, v.H, v.W), dtype=np.float32)
+        for z in range(v.n_out):
+            t = z % v.zfactor
+            if t:
+                rebuilt[z] = table[cy[:, None], cx[None, :], t - 1]
+        assert np.array_equal(rebuilt, var[i].cpu().numpy())
     plan.close()
