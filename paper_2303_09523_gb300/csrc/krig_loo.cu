@@ -83,6 +83,11 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     static_assert(KRIG_LOO_REP == 32, "one copy per lane in the reductions below");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // programmatic dependent launch: let the next kernel of the pass launch.  The
+    // class solve itself reads only the variogram and the geometry, so it runs
+    // before the wait for the previous kernel (overlapping its tail); everything
+    // that touches the pass's accumulators, weights or record runs after the wait.
+    asm volatile("griddepcontrol.launch_dependents;");
     int v = 0;
     for (int u = 1; u < P.n_vols; ++u)
         if (P.vol[u].loo_cls_begin <= blockIdx.x) v = u;
@@ -90,10 +95,10 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     const int local = (int)(blockIdx.x - V.loo_cls_begin);
     const int cy = local / V.ncx, cx = local % V.ncx;
     const krig_variogram vg = P.vg[v];
-    if (mode_in != 1) {
-        // a new pass: zero the volume's loss sums and (backward) the dL/dw sums, spread
-        // over its class blocks; the kernels that add to them run after this launch
-        const int ncls = V.ncx * V.ncy, taps = 2 * (2 * V.r + 1) * (2 * V.r + 1);
+    const int ncls = V.ncx * V.ncy, taps = 2 * (2 * V.r + 1) * (2 * V.r + 1);
+    // a new pass: zero the volume's loss sums and (backward) the dL/dw sums, spread
+    // over its class blocks; the kernels that add to them run after this launch
+    auto zero_pass = [&]() {
         for (int e = local * 256 + tid; e < KRIG_LOO_REP; e += ncls * 256) ((double*)(P.ws + V.lacc_off))[e] = 0.0;
         if (mode_in == 2) {
             for (int e = local * 256 + tid; e < KRIG_LOO_REP * ncls * taps; e += ncls * 256)
@@ -102,11 +107,14 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
                 ((double*)(P.ws + V.lorb_off))[e] = 0.0;
             if (P.grad_params && !P.accumulate && local == 0 && tid < 3) P.grad_params[3 * v + tid] = 0.0;
         }
-    }
+    };
     krig_variogram* rec = (krig_variogram*)(P.ws + V.lvg_off);
-    if (mode_in == 2 && rec->model == vg.model && rec->nugget == vg.nugget && rec->sill == vg.sill &&
-        rec->range == vg.range)
-        return;  // these weights are already in the workspace
+    if (mode_in == 2) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        zero_pass();
+        if (rec->model == vg.model && rec->nugget == vg.nugget && rec->sill == vg.sill && rec->range == vg.range)
+            return;  // these weights are already in the workspace
+    }
     const int mode = mode_in == 1 ? 1 : 0;
     const int r = V.r, n2r = 2 * r + 1, nr = r + 1;
     const int g2 = 2 * V.g;  // LOO: bracketing slices 2g apart, target in the middle
@@ -135,12 +143,8 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     __syncthreads();
     const int lx = V.xext[cx][0], rx = V.xext[cx][1], ly = V.yext[cy][0], ry = V.yext[cy][1];
     const int nx = lx + rx + 1, ny = ly + ry + 1;
-    const int n = nx * ny;                // in-plane points (per slice)
-    const int m = mode == 0 ? 2 : 3;      // right-hand sides: 2c, 2 (ones), [wbar_lo + wbar_up]
+    const int n = nx * ny;  // in-plane points (per slice)
     const int nn = n2r * n2r;
-    const double* lbar = (const double*)(P.ws + V.lbar_off) + (int64_t)local * (2 * nn);
-    const int64_t lrep = (int64_t)V.ncx * V.ncy * (2 * nn);  // stride between the copies
-    const double coef = mode == 0 ? 0.0 : 2.0 * P.grad_loss[v] / ((double)(V.n - 2) * V.H * V.W);
     for (int e = tid; e < nn; e += 256) {
         const double a = gC[e] + gC[nn + e];  // A + B at in-plane lag e
         S.T[0][e] = a;
@@ -150,61 +154,26 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
         S.dy[e] = (int8_t)(e < n ? e / nx - ly : 0);
     }
-    if (mode == 1) {
-        // sum r S_k of each point over both slices and the KRIG_LOO_REP copies: one
-        // warp per point, one copy per lane; the interior orbit sums likewise
-        for (int i = warp; i < n; i += 8) {
-            const int dx = i % nx - lx, dy = i / nx - ly;
-            double t = 0.0;
-            for (int s = 0; s < 2; ++s) t += lbar[lane * lrep + (s * n2r + (dy + r)) * n2r + (dx + r)];
-            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) tsum[i] = t;
-        }
-        if (local == V.cint && warp == 7) {
-            const double* lorb = (const double*)(P.ws + V.lorb_off);
-            for (int o = 0; o < (r + 1) * (r + 2) / 2; ++o) {
-                double t = lorb[lane * KRIG_NORB + o];
-                for (int k = 16; k; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
-                if (lane == 0) osum[o] = t;
-            }
-        }
-        __syncthreads();
-    }
+    // right-hand sides 2c and 2 (ones); the adjoint's third one (wbar) comes after the wait
     for (int i = tid; i < n; i += 256) {
         const int dx = i % nx - lx, dy = i / nx - ly;
         S.B[0][i][0] = 2.0 * g0[abs(dy) * nr + abs(dx)];
         S.B[0][i][1] = 2.0;
-        if (mode == 1) {
-            double sum = tsum[i];
-            if (local == V.cint) {
-                // interior class: the residual kernel kept only orbit sums (both
-                // slices); dL/dtheta depends on wbar only through them (the class
-                // system and its symmetric right-hand sides are D4-invariant), so
-                // each orbit's total is spread evenly over its taps
-                const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy)), o = a * (a + 1) / 2 + b;
-                int cnt = 0;
-                for (int qy = -r; qy <= r; ++qy)
-                    for (int qx = -r; qx <= r; ++qx) {
-                        const int qa = max(abs(qx), abs(qy)), qb = min(abs(qx), abs(qy));
-                        cnt += (qa * (qa + 1) / 2 + qb) == o;
-                    }
-                sum += osum[o] / cnt;
-            }
-            S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
-        }
     }
     if (tid == 0) S.fail = 0;
     __syncthreads();
-    if (warp == 0 && !ds_warp_gj(S, 0, n, m, n2r, &S.X[0][0][0], &S.Ai[0][0][0], lane) && lane == 0) S.fail = 1;
+    if (warp == 0 && !ds_warp_gj(S, 0, n, 2, n2r, &S.X[0][0][0], &S.Ai[0][0][0], lane) && lane == 0) S.fail = 1;
     __syncthreads();
     if (S.fail) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        if (mode_in == 0) zero_pass();
         if (tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         return;
     }
-    // FP64 refinement: R = B - (A+B) X, X += (A+B)^-1 R
-    const int nv = n * m;
-    {
-        const int i = tid / m, c = tid % m;
+    // FP64 refinement of column c: R = B - (A+B) X, X += (A+B)^-1 R (threads i * m + c)
+    auto refine = [&](int c0, int m) {
+        const int nv = n * m;
+        const int i = tid / m, c = c0 + tid % m;
         if (tid < nv) {
             double acc = S.B[0][i][c];
             for (int j = 0; j < n; ++j)
@@ -218,27 +187,26 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
             S.X[0][i][c] += (double)corr;
         }
         __syncthreads();
-    }
-    // sums over the points (one warp: n <= 32): 1's_u, 1's_v, 1's_x
+    };
+    refine(0, 2);
+    // sums over the points (one warp: n <= 32): 1's_u, 1's_v; phi and the weights
     if (warp == 0) {
-        double su = 0.0, sv = 0.0, sx = 0.0;
+        double su = 0.0, sv = 0.0;
         if (lane < n) {
             su = S.X[0][lane][0];
             sv = S.X[0][lane][1];
-            if (mode == 1) sx = S.X[0][lane][2];
         }
         for (int o = 16; o; o >>= 1) {
             su += __shfl_xor_sync(0xffffffffu, su, o);
             sv += __shfl_xor_sync(0xffffffffu, sv, o);
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
         }
-        const double phi = (su - 1.0) / sv, aphi = sx / sv;
-        if (lane < n) {
-            wgt[lane] = 0.5 * (S.X[0][lane][0] - phi * S.X[0][lane][1]);
-            if (mode == 1) abar[lane] = S.X[0][lane][2] - aphi * S.X[0][lane][1];
-        }
+        const double phi = (su - 1.0) / sv;
+        if (lane < n) wgt[lane] = 0.5 * (S.X[0][lane][0] - phi * S.X[0][lane][1]);
+        if (lane == 0) red[0][0] = sv;
     }
     __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous kernel of the pass is complete
+    if (mode_in == 0) zero_pass();
     if (mode == 0) {
         // LOO weight row in the full tap layout [s][dy+r][dx+r] (the same in both
         // slices), zeros on truncated taps
@@ -267,6 +235,63 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         if (tid == 0) *rec = vg;  // read by a later launch only
         return;
     }
+    // adjoint: sum r S_k of each point over both slices and the KRIG_LOO_REP copies
+    // (one warp per point, one copy per lane), the interior orbit sums likewise
+    const double* lbar = (const double*)(P.ws + V.lbar_off) + (int64_t)local * (2 * nn);
+    const int64_t lrep = (int64_t)V.ncx * V.ncy * (2 * nn);  // stride between the copies
+    const double coef = 2.0 * P.grad_loss[v] / ((double)(V.n - 2) * V.H * V.W);
+    for (int i = warp; i < n; i += 8) {
+        const int dx = i % nx - lx, dy = i / nx - ly;
+        double t = 0.0;
+        for (int s2 = 0; s2 < 2; ++s2) t += lbar[lane * lrep + (s2 * n2r + (dy + r)) * n2r + (dx + r)];
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) tsum[i] = t;
+    }
+    if (local == V.cint && warp == 7) {
+        const double* lorb = (const double*)(P.ws + V.lorb_off);
+        for (int o = 0; o < (r + 1) * (r + 2) / 2; ++o) {
+            double t = lorb[lane * KRIG_NORB + o];
+            for (int k = 16; k; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+            if (lane == 0) osum[o] = t;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += 256) {
+        const int dx = i % nx - lx, dy = i / nx - ly;
+        double sum = tsum[i];
+        if (local == V.cint) {
+            // interior class: the residual kernel kept only orbit sums (both
+            // slices); dL/dtheta depends on wbar only through them (the class
+            // system and its symmetric right-hand sides are D4-invariant), so
+            // each orbit's total is spread evenly over its taps
+            const int a = max(abs(dx), abs(dy)), b = min(abs(dx), abs(dy)), o = a * (a + 1) / 2 + b;
+            int cnt = 0;
+            for (int qy = -r; qy <= r; ++qy)
+                for (int qx = -r; qx <= r; ++qx) {
+                    const int qa = max(abs(qx), abs(qy)), qb = min(abs(qx), abs(qy));
+                    cnt += (qa * (qa + 1) / 2 + qb) == o;
+                }
+            sum += osum[o] / cnt;
+        }
+        S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
+    }
+    __syncthreads();
+    // third column by the FP32 inverse of the factorised system, then one FP64 refinement
+    for (int i = tid; i < n; i += 256) {
+        double x = 0.0;
+        for (int j = 0; j < n; ++j) x += (double)S.Ai[0][i][j] * S.B[0][j][2];
+        S.X[0][i][2] = x;
+    }
+    __syncthreads();
+    refine(2, 1);
+    if (warp == 0) {
+        double sx = 0.0;
+        if (lane < n) sx = S.X[0][lane][2];
+        for (int o = 16; o; o >>= 1) sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        const double aphi = sx / red[0][0];
+        if (lane < n) abar[lane] = S.X[0][lane][2] - aphi * S.X[0][lane][1];
+    }
+    __syncthreads();
     // dL/dtheta_p = sum_i abar_i (dc0_i/dtheta_p - sum_j d(A+B)_ij/dtheta_p w_j), i, j over the points
     // eight threads per point i, each over every eighth j
     double tp3[3] = {0.0, 0.0, 0.0};
@@ -675,6 +700,8 @@ template <int R>
 __global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
 {
     extern __shared__ __align__(16) float lsm[];
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the class weights of this pass
     const int64_t it = blockIdx.x;
     int v = 0;
     for (int u = 1; u < P.n_vols; ++u)
@@ -817,6 +844,8 @@ template <int R>
 __global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_grad(const __grid_constant__ KrigLaunch P, int64_t nborder)
 {
     extern __shared__ __align__(16) float lsm[];
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the residuals of this pass
     if ((int64_t)blockIdx.x < nborder) {
         loo_border_block<R>(P, blockIdx.x, lsm);
         return;
@@ -853,22 +882,46 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
     return m;
 }
 
+// Every LOO kernel waits for its predecessor on the stream (griddepcontrol.wait)
+// before it touches the pass's data, so each kernel after the first of a pass
+// is launched early (programmatic dependent launch): its blocks are scheduled
+// while the previous grid drains.  The first kernel of a pass is an ordinary
+// launch: it starts after whatever the caller queued before it (which may
+// write the variogram parameters) has completed, so the kernels chained
+// behind it may read those parameters before their own wait.
+template <typename... KArgs, typename... Args>
+static cudaError_t loo_launch(bool early, void (*kernel)(KArgs...), unsigned grid, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int want_grad_params, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     // the class launch also zeroes the accumulators of the pass
-    k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, backward ? 2 : 0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    if ((e = loo_launch(false, k_loo_class, (unsigned)L.n_loo_classes, 0, st, L, backward ? 2 : 0)) != cudaSuccess) return (int)e;
     bool has_r[KRIG_RMAX + 1] = {};
     for (int v = 0; v < L.n_vols; ++v) has_r[L.vol[v].r] = true;
     const size_t s1 = loo_smem(L, 0);
     for (int r = 0; r <= KRIG_RMAX; ++r) {
         if (!has_r[r]) continue;
-        if (r == 0) k_loo_residual<0><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
-        else if (r == 1) k_loo_residual<1><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
-        else k_loo_residual<2><<<(unsigned)L.n_loo_items, 256, s1, st>>>(L, backward ? 1 : 0);
-        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        const int mode = backward ? 1 : 0;
+        if (r == 0) e = loo_launch(true, k_loo_residual<0>, (unsigned)L.n_loo_items, s1, st, L, mode);
+        else if (r == 1) e = loo_launch(true, k_loo_residual<1>, (unsigned)L.n_loo_items, s1, st, L, mode);
+        else e = loo_launch(true, k_loo_residual<2>, (unsigned)L.n_loo_items, s1, st, L, mode);
+        if (e != cudaSuccess) return (int)e;
     }
     if (!backward) return 0;
     int64_t nb = 0;
@@ -879,15 +932,14 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
         const size_t s2 = loo_smem(L, 1);
         for (int r = 0; r <= KRIG_RMAX; ++r) {
             if (!has_r[r]) continue;
-            if (r == 0) k_loo_grad<0><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
-            else if (r == 1) k_loo_grad<1><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
-            else k_loo_grad<2><<<(unsigned)(nb + na), 256, s2, st>>>(L, nb);
-            if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+            if (r == 0) e = loo_launch(true, k_loo_grad<0>, (unsigned)(nb + na), s2, st, L, nb);
+            else if (r == 1) e = loo_launch(true, k_loo_grad<1>, (unsigned)(nb + na), s2, st, L, nb);
+            else e = loo_launch(true, k_loo_grad<2>, (unsigned)(nb + na), s2, st, L, nb);
+            if (e != cudaSuccess) return (int)e;
         }
     }
     if (want_grad_params) {
-        k_loo_class<<<(unsigned)L.n_loo_classes, 256, 0, st>>>(L, 1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+        if ((e = loo_launch(true, k_loo_class, (unsigned)L.n_loo_classes, 0, st, L, 1)) != cudaSuccess) return (int)e;
     }
     return 0;
 }
