@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkrig.so")
 SOURCES = ["krig_api.cu", "krig_ds_solve.cu", "krig_ds.cu", "krig_ds_f32.cu", "krig_ds_u16.cu", "krig_ds_f64.cu", "krig_voxel.cu", "krig_loo.cu", "krig_noalloc.cu", "krig_peaks.cu", "krig_variogram.cu", "krig_similarity.cu", "krig_mc.cu", "krig_uk.cu"]
-HEADERS = ["krig_internal.h", "krig_device.cuh", "krig_ds_apply.cuh"]
+HEADERS = ["krig_internal.h", "krig_device.cuh", "krig_ds_apply.cuh", "krig_ff.cuh"]
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "krig_internal.h"
+#include "krig_ff.cuh"
 
 // Covariance C(h) = C(0) - gamma(h) at squared lag h2, written so that no
 // cancellation occurs for h > 0.  Spherical: sill (1 - 1.5 q + 0.5 q^3) for
@@ -34,6 +35,7 @@ __device__ __forceinline__ double krig_cov(const krig_variogram& v, double h2)
     }
     return v.sill * exp(-3.0 * h / v.range);
 }
+
 
 // Lag tables of one volume.
 //   gC[s][ay][ax], s in {0,1} (same / other known slice, dz = s*g),
@@ -431,42 +433,68 @@ constexpr int ZL = 32;                                         // register row: 
 static_assert(ZN + 1 + KRIG_GMAX / 2 <= ZL, "register row too short");
 static_assert(ZN * 8 <= 256, "one refinement entry per thread");
 
+constexpr int ZLP = ZL + 4;  // padded row of the augmented matrices: float4-aligned, rows 4 banks apart
+
 struct ZSmem {
-    double T[2][ZN];          // A + B, A - B entries by in-plane lag ay * (2r+1) + ax
-    float Tf[2][ZN];
-    double B[2][ZN][8];       // right-hand sides
-    double X[2][ZN][8];       // solutions
-    float R[2][ZN][8];        // FP64 residuals rounded to FP32
-    float Ai[2][ZN][ZN + 1];  // FP32 inverses, padded rows
-    double W[2][ZN][8];       // weights: [slice][point][t-1]
-    double var[8];            // kriging variance per target
+    ff T[2][ZN];              // A + B, A - B entries by in-plane lag ay * (2r+1) + ax
+    ff B[2][ZN][8];           // right-hand sides
+    ff X[2][ZN][8];           // refined solutions
+    float R[2][ZN][8];        // residuals rounded to FP32
+    ff W[2][ZN][8];           // weights: [slice][point][t-1]
+    float var[8];             // kriging variance per target
+    // [S | B] rows before the factorisation, [X | 0 | S^-1] after (each row
+    // divided by its pivot): X at columns 0..m-1, S^-1 at ZL-n..ZL-1
+    __align__(16) float M[2][ZN][ZLP];
+    __align__(16) float row[2][2][ZL];  // pivot-row broadcast, [system][step parity]
     int8_t dx[ZL], dy[ZL];
     int fail;
 };
 
-// Gauss-Jordan on [S | B] by one warp, lane i holding row i in registers.
-// Each step drops the pivot column from the front of every row and appends
-// the identity column it turns into, so that every register index is static:
-// after n steps a row holds [X | 0 | S^-1] (up to the row's pivot, divided out
-// at the end).  No pivoting (S is SPD); a pivot that is not positive fails.
-__device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, int n2r, double* X, float* Ai, int lane)
+// Row i of the augmented system z in FP32: the system entries (from the lag
+// table T), then the m right-hand sides, then zeros.  All threads of the block
+// fill the rows (e over 2 * ZN * ZL) before the factorisation.
+__device__ __forceinline__ void ds_fill_rows(ZSmem& S, int nsys, int n, const int* msys, int n2r, int tid, int nt)
+{
+    for (int e = tid; e < nsys * n * ZL; e += nt) {
+        const int j = e % ZL, i = (e / ZL) % n, z = e / (ZL * n);
+        float a = 0.0f;
+        if (j < n) a = S.T[z][abs(S.dy[i] - S.dy[j]) * n2r + abs(S.dx[i] - S.dx[j])].hi;
+        else if (j < n + msys[z]) a = S.B[z][i][j - n].hi;
+        S.M[z][i][j] = a;
+    }
+}
+
+// Gauss-Jordan on the rows of S.M[z] by one warp, lane i holding row i in
+// registers.  Each step drops the pivot column from the front of every row and
+// appends the identity column it turns into, so that every register index is
+// static: after n steps a row holds [X | 0 | S^-1] (up to the row's pivot,
+// divided out at the end), stored back in place.  The pivot row reaches the
+// other lanes through shared memory (one buffer per step parity: a step's
+// stores cannot overtake the previous step's reads).  No pivoting (S is SPD);
+// a pivot that is not positive fails.
+__device__ __forceinline__ bool ds_warp_gj(ZSmem& S, int z, int n, int lane)
 {
     float r[ZL];
-    const bool row = lane < n;
-    const int dxi = row ? S.dx[lane] : 0, dyi = row ? S.dy[lane] : 0;
+    const float4* src = reinterpret_cast<const float4*>(S.M[z][lane < n ? lane : 0]);
 #pragma unroll
-    for (int j = 0; j < ZL; ++j) {
-        float a = 0.0f;
-        if (row) {
-            if (j < n) a = S.Tf[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])];
-            else if (j < n + m) a = (float)S.B[z][lane][j - n];
-        }
-        r[j] = a;
+    for (int q = 0; q < ZL / 4; ++q) {
+        const float4 v = lane < n ? src[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r[4 * q] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
     }
     float dk = 1.0f;
     bool ok = true;
     for (int k = 0; k < n; ++k) {
-        const float p0 = __shfl_sync(0xffffffffu, r[0], k);
+        float4* buf = reinterpret_cast<float4*>(S.row[z][k & 1]);
+        if (lane == k) {
+#pragma unroll
+            for (int q = 0; q < ZL / 4; ++q) buf[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        }
+        __syncwarp();
+        const float4 v0 = buf[0];
+        const float p0 = v0.x;
         if (!(p0 > 0.0f)) {  // the same value in every lane
             ok = false;
             break;
@@ -475,20 +503,25 @@ __device__ __forceinline__ bool ds_warp_gj(const ZSmem& S, int z, int n, int m, 
         const float fi = r[0] * __frcp_rn(p0);
         const float f = piv ? 0.0f : fi;
         if (piv) dk = p0;
+        r[0] = fmaf(-f, v0.y, r[1]);
+        r[1] = fmaf(-f, v0.z, r[2]);
+        r[2] = fmaf(-f, v0.w, r[3]);
 #pragma unroll
-        for (int j = 0; j + 1 < ZL; ++j) {
-            const float pj = __shfl_sync(0xffffffffu, r[j + 1], k);
-            r[j] = fmaf(-f, pj, r[j + 1]);
+        for (int q = 1; q < ZL / 4; ++q) {
+            const float4 v = buf[q];
+            r[4 * q - 1] = fmaf(-f, v.x, r[4 * q]);
+            r[4 * q] = fmaf(-f, v.y, r[4 * q + 1]);
+            r[4 * q + 1] = fmaf(-f, v.z, r[4 * q + 2]);
+            r[4 * q + 2] = fmaf(-f, v.w, r[4 * q + 3]);
         }
         r[ZL - 1] = piv ? 1.0f : -fi;
     }
-    if (ok && row) {
+    if (ok && lane < n) {
         const float di = 1.0f / dk;
+        float4* dst = reinterpret_cast<float4*>(S.M[z][lane]);
 #pragma unroll
-        for (int j = 0; j < ZL; ++j) {
-            if (j < m) X[lane * 8 + j] = (double)(r[j] * di);
-            if (j >= ZL - n) Ai[lane * (ZN + 1) + j - (ZL - n)] = r[j] * di;
-        }
+        for (int q = 0; q < ZL / 4; ++q)
+            dst[q] = make_float4(r[4 * q] * di, r[4 * q + 1] * di, r[4 * q + 2] * di, r[4 * q + 3] * di);
     }
     return ok;
 }

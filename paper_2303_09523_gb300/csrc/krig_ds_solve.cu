@@ -161,47 +161,55 @@ __device__ __forceinline__ void ds_pair(int idx, int* a, int* b)
 // evaluation per distinct lag: the in-plane part of a lag depends only on
 // (max, min) of |dx|, |dy|, and the upper-slice target lags (dz = g - t)
 // repeat the lower-slice ones (dz = t).
+__device__ __forceinline__ int ds_lag_h2(const LagDims& d, int e, int nCp, int n0p)
+{
+    int a, b, dz;
+    if (e < 2 * nCp) {
+        ds_pair(e % nCp, &a, &b);
+        dz = (e / nCp) * d.g;
+    } else {
+        const int f = e - 2 * nCp;
+        ds_pair(f % n0p, &a, &b);
+        dz = f / n0p + 1;
+    }
+    return a * a + b * b + dz * dz;
+}
 __device__ void ds_eval_lags(const LagDims& d, const krig_variogram& v, double* ev, int tid, int nt)
 {
     const int nCp = d.n2r * (d.n2r + 1) / 2, n0p = d.nr * (d.nr + 1) / 2;
     const int ne = 2 * nCp + (d.g - 1) * n0p;
-    for (int e = tid; e < ne; e += nt) {
-        int a, b;
-        double dz;
-        if (e < 2 * nCp) {
-            ds_pair(e % nCp, &a, &b);
-            dz = (double)((e / nCp) * d.g);
-        } else {
-            const int f = e - 2 * nCp;
-            ds_pair(f % n0p, &a, &b);
-            dz = (double)(f / n0p + 1);
-        }
-        ev[e] = krig_cov(v, (double)(a * a + b * b) + dz * dz);
-    }
+    for (int e = tid; e < ne; e += nt) ev[e] = krig_cov(v, (double)ds_lag_h2(d, e, nCp, n0p));
     __syncthreads();
 }
-
+// The same values as float-float pairs (the FP32 class solve).
+__device__ void ds_eval_lags_ff(const LagDims& d, const krig_variogram& v, ff* ev, int tid, int nt)
+{
+    const int nCp = d.n2r * (d.n2r + 1) / 2, n0p = d.nr * (d.nr + 1) / 2;
+    const int ne = 2 * nCp + (d.g - 1) * n0p;
+    for (int e = tid; e < ne; e += nt) ev[e] = ff_from_double(krig_cov(v, (double)ds_lag_h2(d, e, nCp, n0p)));
+    __syncthreads();
+}
 // Covariances from the distinct-lag table: between two points of the window
 // (slice s = same / other, in-plane offsets ay, ax in [0, 2r]) and between a
 // point (slice s, offsets in [0, r]) and target t.
+template <typename E>
 struct DsLags {
-    const double* ev;
+    const E* ev;
     int nCp, n0p, g;
-    __device__ __forceinline__ DsLags(const LagDims& d, const double* e)
+    __device__ __forceinline__ DsLags(const LagDims& d, const E* e)
         : ev(e), nCp(d.n2r * (d.n2r + 1) / 2), n0p(d.nr * (d.nr + 1) / 2), g(d.g) {}
     __device__ __forceinline__ static int pair(int ay, int ax)
     {
         const int a = max(ax, ay), b = min(ax, ay);
         return a * (a + 1) / 2 + b;
     }
-    __device__ __forceinline__ double c(int s, int ay, int ax) const { return ev[s * nCp + pair(ay, ax)]; }
-    __device__ __forceinline__ double c0(int t, int s, int ay, int ax) const
+    __device__ __forceinline__ E c(int s, int ay, int ax) const { return ev[s * nCp + pair(ay, ax)]; }
+    __device__ __forceinline__ E c0(int t, int s, int ay, int ax) const
     {
         const int dz = s == 0 ? t : g - t;
         return ev[2 * nCp + (dz - 1) * n0p + pair(ay, ax)];
     }
 };
-
 // The same values expanded into the lag tables gC, g0 (layout of krig_fill_lags).
 __device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* gC, double* g0, double* ev, int tid,
                              int nt)
@@ -223,10 +231,18 @@ __device__ void ds_fill_lags(const LagDims& d, const krig_variogram& v, double* 
     }
     __syncthreads();
 }
-
-// Solve, combine and write one truncation class (FP32 factorisation).
+// One weight-table entry: FP64 volumes take the pair's value, FP32 volumes its
+// nearest float, u16 volumes the weight times the intensity scale (rounded once).
+__device__ __forceinline__ void ds_store_weight(const KrigVol& V, float* tf, double* td, int64_t i, ff w)
+{
+    if (V.dtype == KRIG_F64) td[i] = ff_to_double(w);
+    else if (V.dtype == KRIG_U16) tf[i] = ff_round(ff_mul_f(w, V.scale));
+    else tf[i] = ff_round(w);
+}
+// Solve, combine and write one truncation class: FP32 factorisation, the
+// residual, the combine and the tables in float-float.
 template <int NT>
-__device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, int cx, const DsLags& lg, ZSmem& S,
+__device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, int cx, const DsLags<ff>& lg, ZSmem& S,
                                 int tid)
 {
     const int warp = tid >> 5, lane = tid & 31;
@@ -237,11 +253,9 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
     const int m0 = 1 + hp, m1 = hm;  // columns of the sum / difference system
     // system entries by lag, points, right-hand sides
     for (int e = tid; e < n2r * n2r; e += NT) {
-        const double a = lg.c(0, e / n2r, e % n2r), b = lg.c(1, e / n2r, e % n2r);
-        S.T[0][e] = a + b;
-        S.T[1][e] = a - b;
-        S.Tf[0][e] = (float)(a + b);
-        S.Tf[1][e] = (float)(a - b);
+        const ff a = lg.c(0, e / n2r, e % n2r), b = lg.c(1, e / n2r, e % n2r);
+        S.T[0][e] = ff_add(a, b);
+        S.T[1][e] = ff_sub(a, b);
     }
     for (int e = tid; e < ZL; e += NT) {
         S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
@@ -250,42 +264,43 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
     for (int e = tid; e < n * 8; e += NT) {
         const int i = e >> 3, c = e & 7;
         const int ax = abs(i % nx - lx), ay = abs(i / nx - ly);
-        double bp = 0.0, bm = 0.0;
-        if (c == 0) bp = 2.0;
-        else if (c <= hp) bp = lg.c0(c, 0, ay, ax) + lg.c0(c, 1, ay, ax);
-        if (c < hm) bm = lg.c0(c + 1, 0, ay, ax) - lg.c0(c + 1, 1, ay, ax);
+        ff bp = ff_make(0.0f), bm = ff_make(0.0f);
+        if (c == 0) bp = ff_make(2.0f);
+        else if (c <= hp) bp = ff_add(lg.c0(c, 0, ay, ax), lg.c0(c, 1, ay, ax));
+        if (c < hm) bm = ff_sub(lg.c0(c + 1, 0, ay, ax), lg.c0(c + 1, 1, ay, ax));
         S.B[0][i][c] = bp;
         S.B[1][i][c] = bm;
     }
     if (tid == 0) S.fail = 0;
     __syncthreads();
+    const int msys[2] = {m0, m1};
+    ds_fill_rows(S, m1 > 0 ? 2 : 1, n, msys, n2r, tid, NT);
+    __syncthreads();
     // FP32 factorisation: the sum system on warp 0, the difference system on warp 1
     if (warp < 2 && (warp == 0 || m1 > 0)) {
-        const int z = warp;
-        if (!ds_warp_gj(S, z, n, z ? m1 : m0, n2r, &S.X[z][0][0], &S.Ai[z][0][0], lane) && lane == 0) S.fail = 1;
+        if (!ds_warp_gj(S, warp, n, lane) && lane == 0) S.fail = 1;
     }
     __syncthreads();
     const bool ok = !S.fail;
-    // FP64 refinement: R = B - S X in FP64, X += S^-1 R in FP32
+    // refinement: R = B - S X (compensated), X += S^-1 R in FP32, X kept as a pair
     const int nv = n * (m0 + m1);  // (system, point, column) triples
     if (ok) {
         // one (system, point, column) per thread: nv <= ZN * 8 <= NT
         const int z = tid < n * m0 ? 0 : 1, f = z ? tid - n * m0 : tid, m = z ? m1 : m0;
         const int i = m ? f / m : 0, c = m ? f % m : 0;
-        float res = 0.0f;
         if (tid < nv) {
             const int dxi = S.dx[i], dyi = S.dy[i];
-            double acc = S.B[z][i][c];
+            ff_dot acc(S.B[z][i][c]);
             for (int j = 0; j < n; ++j)
-                acc = fma(-S.T[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])], S.X[z][j][c], acc);
-            res = (float)acc;
+                acc.add(S.T[z][abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j])], -S.M[z][j][c]);
+            S.R[z][i][c] = ff_round(acc.value());
         }
-        if (tid < nv) S.R[z][i][c] = res;
         __syncthreads();
         if (tid < nv) {
+            const float* ai = &S.M[z][i][ZL - n];  // row i of S^-1
             float corr = 0.0f;
-            for (int j = 0; j < n; ++j) corr = fmaf(S.Ai[z][i][j], S.R[z][j][c], corr);
-            S.X[z][i][c] += (double)corr;
+            for (int j = 0; j < n; ++j) corr = fmaf(ai[j], S.R[z][j][c], corr);
+            S.X[z][i][c] = ff_two_sum(S.M[z][i][c], corr);
         }
         __syncthreads();
         // combine, one warp per target t (lane = point):
@@ -294,25 +309,23 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
         if (warp < g - 1) {
             const int t = warp + 1, p = min(t, g - t);
             const bool in = lane < n;
-            const double sv = in ? S.X[0][lane][0] : 0.0, st = in ? S.X[0][lane][p] : 0.0;
-            double sd = 0.0;
-            if (in && t != g - t) sd = (t < g - t ? 1.0 : -1.0) * S.X[1][lane][p - 1];
-            double a = sv, b = st;
-            for (int o = 16; o; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                b += __shfl_xor_sync(0xffffffffu, b, o);
-            }
-            const double ph = (b - 1.0) / a;
-            const double w0 = 0.5 * (st + sd) - 0.5 * ph * sv, w1 = 0.5 * (st - sd) - 0.5 * ph * sv;
-            double wc = 0.0;
+            const ff zero = ff_make(0.0f);
+            const ff sv = in ? S.X[0][lane][0] : zero, st = in ? S.X[0][lane][p] : zero;
+            ff sd = zero;
+            if (in && t != g - t) sd = t < g - t ? S.X[1][lane][p - 1] : ff_neg(S.X[1][lane][p - 1]);
+            const ff a = ff_warp_sum(sv), b = ff_warp_sum(st);
+            const ff ph = ff_div(ff_sub(b, ff_make(1.0f)), a);
+            const ff hv = ff_scale2(ff_mul(ph, sv), 0.5f);
+            const ff w0 = ff_sub(ff_scale2(ff_add(st, sd), 0.5f), hv), w1 = ff_sub(ff_scale2(ff_sub(st, sd), 0.5f), hv);
+            ff wc = zero;
             if (in) {
                 const int ax = abs(S.dx[lane]), ay = abs(S.dy[lane]);
-                wc = w0 * lg.c0(t, 0, ay, ax) + w1 * lg.c0(t, 1, ay, ax);
+                wc = ff_add(ff_mul(w0, lg.c0(t, 0, ay, ax)), ff_mul(w1, lg.c0(t, 1, ay, ax)));
                 S.W[0][lane][t - 1] = w0;
                 S.W[1][lane][t - 1] = w1;
             }
-            for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-            if (lane == 0) S.var[t - 1] = lg.c(0, 0, 0) - wc - ph;
+            wc = ff_warp_sum(wc);
+            if (lane == 0) S.var[t - 1] = ff_round(ff_sub(ff_sub(lg.c(0, 0, 0), wc), ph));
         }
         __syncthreads();
     } else if (tid == 0) {
@@ -321,17 +334,14 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
     // weight-table row of the class: [s][dy+r][dx+r][t slot], zeros on
     // truncated taps and unused t slots; u16 input: weights carry the scale
     const int n2 = n2r * n2r, ntap = 2 * n2;
-    const double scale = V.dtype == KRIG_U16 ? (double)V.scale : 1.0;
-    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     const int64_t row = ((int64_t)cy * V.ncx + cx) * ntap * KRIG_TSLOTS;
     for (int e = tid; e < ntap * KRIG_TSLOTS; e += NT) {
         const int c = e % KRIG_TSLOTS, f = e / KRIG_TSLOTS;
         const int dx = f % n2r - r, dy = (f / n2r) % n2r - r, s = f / n2;
-        double w = 0.0;
+        ff w = ff_make(0.0f);
         if (c < g - 1 && dx >= -lx && dx <= rx && dy >= -ly && dy <= ry)
-            w = ok ? S.W[s][(dy + ly) * nx + dx + lx][c] * scale : qnan;
-        if (V.dtype == KRIG_F64) ((double*)(P.ws + V.wtab_off))[row + e] = w;
-        else ((float*)(P.ws + V.wtab_off))[row + e] = (float)w;
+            w = ok ? S.W[s][(dy + ly) * nx + dx + lx][c] : ff_make(__int_as_float(0x7fc00000));
+        ds_store_weight(V, (float*)(P.ws + V.wtab_off), (double*)(P.ws + V.wtab_off), row + e, w);
     }
     // interior class: weight per D4 orbit.  The class is D4-symmetric, so the
     // members of an orbit carry the same weight up to rounding; the table takes
@@ -339,22 +349,20 @@ __device__ void ds_class_zsplit(const KrigLaunch& P, const KrigVol& V, int cy, i
     if (cy * V.ncx + cx == V.cint) {
         for (int e = tid; e < 2 * KRIG_NORB * KRIG_TSLOTS; e += NT) {
             const int c = e % KRIG_TSLOTS, o = (e / KRIG_TSLOTS) % KRIG_NORB, s = e / (KRIG_TSLOTS * KRIG_NORB);
-            double w = 0.0;
+            ff w = ff_make(0.0f);
             if (c < g - 1 && o < (r + 1) * (r + 2) / 2) {
                 int oa, ob;
                 ds_pair(o, &oa, &ob);
-                w = ok ? S.W[s][(ob + ly) * nx + oa + lx][c] * scale : qnan;
+                w = ok ? S.W[s][(ob + ly) * nx + oa + lx][c] : ff_make(__int_as_float(0x7fc00000));
             }
-            if (V.dtype == KRIG_F64) ((double*)(P.ws + V.otab_off))[e] = w;
-            else ((float*)(P.ws + V.otab_off))[e] = (float)w;
+            ds_store_weight(V, (float*)(P.ws + V.otab_off), (double*)(P.ws + V.otab_off), e, w);
         }
     }
     if (tid < KRIG_TSLOTS) {
         float* vt = (float*)(P.ws + V.vtab_off) + ((int64_t)cy * V.ncx + cx) * KRIG_TSLOTS;
-        vt[tid] = (tid < g - 1) ? (ok ? (float)S.var[tid] : __int_as_float(0x7fc00000)) : 0.0f;
+        vt[tid] = (tid < g - 1) ? (ok ? S.var[tid] : __int_as_float(0x7fc00000)) : 0.0f;
     }
 }
-
 template <typename TF>
 __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLaunch P)
 {
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     __shared__ double gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
     __shared__ double g0[(KRIG_GMAX - 1) * 2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
     __shared__ double phi[8], vout[8];
-    __shared__ double ev[ZEV];
+    __shared__ __align__(8) unsigned char evb[ZEV * 8];  // distinct-lag covariances: double or pair
 
     const int tid = threadIdx.x;
     // the stencil's frame-unit tickets start from zero (it reads them after this grid completes)
@@ -379,15 +387,15 @@ __global__ void __launch_bounds__(256) k_ds_solve(const __grid_constant__ KrigLa
     const int r = V.r;
     LagDims d{r, V.g, 2 * r + 1, r + 1};
     if (sizeof(TF) == 8) {
-        ds_fill_lags(d, vg, gC, g0, ev, tid, 256);
+        ds_fill_lags(d, vg, gC, g0, (double*)evb, tid, 256);
         SolveSmem<double, KRIG_KMAX, 8>& S = U.f64;
         const int K = ds_class_setup(V, d, g0, cy, cx, S.tap, S.Bd);
         const bool ok = team_ok_solve<double, KRIG_KMAX, 8, 256>(S, d, gC, K, V.g, tid);
         if (!ok && tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         ds_write_class(P, V, cy, cx, ok, S.Xd, S.Bd, S.tap, K, V.g, gC[0], phi, vout);
     } else {
-        ds_eval_lags(d, vg, ev, tid, 256);
-        ds_class_zsplit<256>(P, V, cy, cx, DsLags(d, ev), U.z, tid);
+        ds_eval_lags_ff(d, vg, (ff*)evb, tid, 256);
+        ds_class_zsplit<256>(P, V, cy, cx, DsLags<ff>(d, (const ff*)evb), U.z, tid);
     }
 }
 

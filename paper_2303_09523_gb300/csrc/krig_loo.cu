@@ -56,6 +56,11 @@ __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2
     }
 }
 
+__device__ __forceinline__ bool loo_same_bits(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
 // ---------------------------------------------------------------------------
 // Class kernel: one block per (volume, xy-class).  mode 0: LOO weights (and
 // a record of the variogram they were solved for).  mode 2: the same, unless
@@ -70,16 +75,20 @@ __device__ __forceinline__ void krig_cov_grad(const krig_variogram& v, double h2
 // dL/dtheta, sum_i abar_i (dc0_i - (dC w)_i) runs over both slices with equal
 // brackets, so only abar_lower + abar_upper = s_x - (1's_x / 1's_v) s_v enters,
 // with s_x from the same sum system at right-hand side wbar_lower + wbar_upper.
+// Arithmetic: covariances in FP64, FP32 factorisation, residuals, combine and
+// adjoint in float-float (this GPU's FP64 rate is 1/64 of FP32); the dL/dtheta
+// sums leave in FP64.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigLaunch P, int mode_in)
 {
     __shared__ ZSmem S;
-    __shared__ double gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
-    __shared__ double g0[2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
-    __shared__ double dC[3][2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
-    __shared__ double d0[3][2 * (KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
-    __shared__ double wgt[ZN], abar[ZN], red[8][4];
-    __shared__ double tsum[ZN], osum[KRIG_NORB];  // mode 1: tap and orbit sums over the copies
+    __shared__ ff gC[2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
+    __shared__ ff g0[(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
+    __shared__ ff dC[3][2 * (2 * KRIG_RMAX + 1) * (2 * KRIG_RMAX + 1)];
+    __shared__ ff d0[3][(KRIG_RMAX + 1) * (KRIG_RMAX + 1)];
+    __shared__ ff wgt[ZN], abar[ZN], red[8][4];
+    __shared__ ff tsum[ZN], osum[KRIG_NORB];  // mode 1: tap and orbit sums over the copies
+    __shared__ ff svs;                        // 1's_v
     static_assert(KRIG_LOO_REP == 32, "one copy per lane in the reductions below");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -112,31 +121,36 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     if (mode_in == 2) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
         zero_pass();
-        if (rec->model == vg.model && rec->nugget == vg.nugget && rec->sill == vg.sill && rec->range == vg.range)
+        if (rec->model == vg.model && loo_same_bits(rec->nugget, vg.nugget) && loo_same_bits(rec->sill, vg.sill) &&
+            loo_same_bits(rec->range, vg.range))
             return;  // these weights are already in the workspace
     }
     const int mode = mode_in == 1 ? 1 : 0;
     const int r = V.r, n2r = 2 * r + 1, nr = r + 1;
     const int g2 = 2 * V.g;  // LOO: bracketing slices 2g apart, target in the middle
-    const int nC = 2 * n2r * n2r, n0 = 2 * nr * nr;
+    const int nC = 2 * n2r * n2r, n0 = nr * nr;
+    // covariances (and, in the adjoint pass, their derivatives) in FP64, kept as pairs
     for (int e = tid; e < nC + n0; e += 256) {
-        double h2, dd[3];
+        int h2;
+        double dd[3];
         if (e < nC) {
             const int ax = e % n2r, ay = (e / n2r) % n2r, s = e / (n2r * n2r);
-            h2 = (double)(ax * ax + ay * ay) + (double)(s * g2) * (double)(s * g2);
-            gC[e] = krig_cov(vg, h2);
-            if (mode == 1) {  // covariance derivatives: the adjoint pass only
-                krig_cov_grad(vg, h2, dd);
-                for (int p = 0; p < 3; ++p) dC[p][e] = dd[p];
+            h2 = ax * ax + ay * ay + (s * g2) * (s * g2);
+            gC[e] = ff_from_double(krig_cov(vg, (double)h2));
+            if (mode == 1) {
+                krig_cov_grad(vg, (double)h2, dd);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) dC[p][e] = ff_from_double(dd[p]);
             }
         } else {
             const int f = e - nC;
-            const int ax = f % nr, ay = (f / nr) % nr;
-            h2 = (double)(ax * ax + ay * ay) + (double)V.g * (double)V.g;  // dz = g both sides
-            g0[f] = krig_cov(vg, h2);
+            const int ax = f % nr, ay = f / nr;
+            h2 = ax * ax + ay * ay + V.g * V.g;  // dz = g both sides
+            g0[f] = ff_from_double(krig_cov(vg, (double)h2));
             if (mode == 1) {
-                krig_cov_grad(vg, h2, dd);
-                for (int p = 0; p < 3; ++p) d0[p][f] = dd[p];
+                krig_cov_grad(vg, (double)h2, dd);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) d0[p][f] = ff_from_double(dd[p]);
             }
         }
     }
@@ -145,11 +159,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     const int nx = lx + rx + 1, ny = ly + ry + 1;
     const int n = nx * ny;  // in-plane points (per slice)
     const int nn = n2r * n2r;
-    for (int e = tid; e < nn; e += 256) {
-        const double a = gC[e] + gC[nn + e];  // A + B at in-plane lag e
-        S.T[0][e] = a;
-        S.Tf[0][e] = (float)a;
-    }
+    for (int e = tid; e < nn; e += 256) S.T[0][e] = ff_add(gC[e], gC[nn + e]);  // A + B at in-plane lag e
     for (int e = tid; e < ZL; e += 256) {
         S.dx[e] = (int8_t)(e < n ? e % nx - lx : 0);
         S.dy[e] = (int8_t)(e < n ? e / nx - ly : 0);
@@ -157,12 +167,15 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
     // right-hand sides 2c and 2 (ones); the adjoint's third one (wbar) comes after the wait
     for (int i = tid; i < n; i += 256) {
         const int dx = i % nx - lx, dy = i / nx - ly;
-        S.B[0][i][0] = 2.0 * g0[abs(dy) * nr + abs(dx)];
-        S.B[0][i][1] = 2.0;
+        S.B[0][i][0] = ff_scale2(g0[abs(dy) * nr + abs(dx)], 2.0f);
+        S.B[0][i][1] = ff_make(2.0f);
     }
     if (tid == 0) S.fail = 0;
     __syncthreads();
-    if (warp == 0 && !ds_warp_gj(S, 0, n, 2, n2r, &S.X[0][0][0], &S.Ai[0][0][0], lane) && lane == 0) S.fail = 1;
+    const int msys[2] = {2, 0};
+    ds_fill_rows(S, 1, n, msys, n2r, tid, 256);
+    __syncthreads();
+    if (warp == 0 && !ds_warp_gj(S, 0, n, lane) && lane == 0) S.fail = 1;
     __syncthreads();
     if (S.fail) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -170,39 +183,35 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         if (tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
         return;
     }
-    // FP64 refinement of column c: R = B - (A+B) X, X += (A+B)^-1 R (threads i * m + c)
+    // refinement of columns c0..c0+m-1 (threads i * m + c): R = B - (A+B) X
+    // compensated, X += (A+B)^-1 R in FP32, X kept as a pair
     auto refine = [&](int c0, int m) {
         const int nv = n * m;
         const int i = tid / m, c = c0 + tid % m;
         if (tid < nv) {
-            double acc = S.B[0][i][c];
+            ff_dot acc(S.B[0][i][c]);
             for (int j = 0; j < n; ++j)
-                acc = fma(-S.T[0][abs(S.dy[i] - S.dy[j]) * n2r + abs(S.dx[i] - S.dx[j])], S.X[0][j][c], acc);
-            S.R[0][i][c] = (float)acc;
+                acc.add(S.T[0][abs(S.dy[i] - S.dy[j]) * n2r + abs(S.dx[i] - S.dx[j])], -S.M[0][j][c]);
+            S.R[0][i][c] = ff_round(acc.value());
         }
         __syncthreads();
         if (tid < nv) {
+            const float* ai = &S.M[0][i][ZL - n];  // row i of (A+B)^-1
             float corr = 0.0f;
-            for (int j = 0; j < n; ++j) corr = fmaf(S.Ai[0][i][j], S.R[0][j][c], corr);
-            S.X[0][i][c] += (double)corr;
+            for (int j = 0; j < n; ++j) corr = fmaf(ai[j], S.R[0][j][c], corr);
+            S.X[0][i][c] = ff_two_sum(S.M[0][i][c], corr);
         }
         __syncthreads();
     };
     refine(0, 2);
     // sums over the points (one warp: n <= 32): 1's_u, 1's_v; phi and the weights
     if (warp == 0) {
-        double su = 0.0, sv = 0.0;
-        if (lane < n) {
-            su = S.X[0][lane][0];
-            sv = S.X[0][lane][1];
-        }
-        for (int o = 16; o; o >>= 1) {
-            su += __shfl_xor_sync(0xffffffffu, su, o);
-            sv += __shfl_xor_sync(0xffffffffu, sv, o);
-        }
-        const double phi = (su - 1.0) / sv;
-        if (lane < n) wgt[lane] = 0.5 * (S.X[0][lane][0] - phi * S.X[0][lane][1]);
-        if (lane == 0) red[0][0] = sv;
+        const ff zero = ff_make(0.0f);
+        const ff xu = lane < n ? S.X[0][lane][0] : zero, xv = lane < n ? S.X[0][lane][1] : zero;
+        const ff su = ff_warp_sum(xu), sv = ff_warp_sum(xv);
+        const ff phi = ff_div(ff_sub(su, ff_make(1.0f)), sv);
+        if (lane < n) wgt[lane] = ff_scale2(ff_sub(xu, ff_mul(phi, xv)), 0.5f);
+        if (lane == 0) svs = sv;
     }
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous kernel of the pass is complete
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         for (int f = tid; f < 2 * nn; f += 256) {
             const int dx = f % n2r - r, dy = (f / n2r) % n2r - r;
             float w = 0.0f;
-            if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = (float)wgt[(dy + ly) * nx + (dx + lx)];
+            if (dx >= -lx && dx <= rx && dy >= -ly && dy <= ry) w = ff_round(wgt[(dy + ly) * nx + (dx + lx)]);
             lw[f] = w;
         }
         if (local == V.cint && tid < (r + 1) * (r + 2) / 2) {
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
                 for (int dx = -r; dx <= r; ++dx) {
                     const int qa = max(abs(dx), abs(dy)), qb = min(abs(dx), abs(dy));
                     if (qa * (qa + 1) / 2 + qb == tid) {
-                        sum += (float)wgt[(dy + r) * n2r + (dx + r)];
+                        sum += ff_round(wgt[(dy + r) * n2r + (dx + r)]);
                         ++cnt;
                     }
                 }
@@ -236,29 +245,34 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
         return;
     }
     // adjoint: sum r S_k of each point over both slices and the KRIG_LOO_REP copies
-    // (one warp per point, one copy per lane), the interior orbit sums likewise
+    // (one warp per point, one copy per lane), the interior orbit sums likewise;
+    // the FP64 partial sums enter at FP32 precision (relative 6e-8 each)
     const double* lbar = (const double*)(P.ws + V.lbar_off) + (int64_t)local * (2 * nn);
     const int64_t lrep = (int64_t)V.ncx * V.ncy * (2 * nn);  // stride between the copies
-    const double coef = 2.0 * P.grad_loss[v] / ((double)(V.n - 2) * V.H * V.W);
     for (int i = warp; i < n; i += 8) {
         const int dx = i % nx - lx, dy = i / nx - ly;
-        double t = 0.0;
-        for (int s2 = 0; s2 < 2; ++s2) t += lbar[lane * lrep + (s2 * n2r + (dy + r)) * n2r + (dx + r)];
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) tsum[i] = t;
+        const int k0 = (dy + r) * n2r + (dx + r);
+        const ff t = ff_two_sum(__double2float_rn(lbar[lane * lrep + k0]),
+                                __double2float_rn(lbar[lane * lrep + n2r * n2r + k0]));
+        const ff ts = ff_warp_sum(t);
+        if (lane == 0) tsum[i] = ts;
     }
     if (local == V.cint && warp == 7) {
         const double* lorb = (const double*)(P.ws + V.lorb_off);
         for (int o = 0; o < (r + 1) * (r + 2) / 2; ++o) {
-            double t = lorb[lane * KRIG_NORB + o];
-            for (int k = 16; k; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+            const ff t = ff_warp_sum(ff_make(__double2float_rn(lorb[lane * KRIG_NORB + o])));
             if (lane == 0) osum[o] = t;
         }
     }
     __syncthreads();
+    // wbar = 2 gL / N * sum r S_k over both slices, N = (n - 2) H W
+    const int64_t nvox = (int64_t)(V.n - 2) * V.H * V.W;
+    const float nh = (float)nvox;  // N as an exact pair
+    const ff nf = {nh, (float)(nvox - (int64_t)nh)};
+    const ff coef = ff_div(ff_scale2(ff_from_double(P.grad_loss[v]), 2.0f), nf);
     for (int i = tid; i < n; i += 256) {
         const int dx = i % nx - lx, dy = i / nx - ly;
-        double sum = tsum[i];
+        ff sum = tsum[i];
         if (local == V.cint) {
             // interior class: the residual kernel kept only orbit sums (both
             // slices); dL/dtheta depends on wbar only through them (the class
@@ -271,54 +285,60 @@ __global__ void __launch_bounds__(256) k_loo_class(const __grid_constant__ KrigL
                     const int qa = max(abs(qx), abs(qy)), qb = min(abs(qx), abs(qy));
                     cnt += (qa * (qa + 1) / 2 + qb) == o;
                 }
-            sum += osum[o] / cnt;
+            sum = ff_add(sum, ff_div(osum[o], ff_make((float)cnt)));
         }
-        S.B[0][i][2] = coef * sum;  // wbar = 2 gL / N * sum r S_k, both slices
+        S.B[0][i][2] = ff_mul(coef, sum);
     }
     __syncthreads();
-    // third column by the FP32 inverse of the factorised system, then one FP64 refinement
+    // third column by the FP32 inverse of the factorised system, then one refinement
     for (int i = tid; i < n; i += 256) {
-        double x = 0.0;
-        for (int j = 0; j < n; ++j) x += (double)S.Ai[0][i][j] * S.B[0][j][2];
-        S.X[0][i][2] = x;
+        const float* ai = &S.M[0][i][ZL - n];
+        float x = 0.0f;
+        for (int j = 0; j < n; ++j) x = fmaf(ai[j], S.B[0][j][2].hi, x);
+        S.M[0][i][2] = x;  // column 2 of the solved rows
     }
     __syncthreads();
     refine(2, 1);
     if (warp == 0) {
-        double sx = 0.0;
-        if (lane < n) sx = S.X[0][lane][2];
-        for (int o = 16; o; o >>= 1) sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        const double aphi = sx / red[0][0];
-        if (lane < n) abar[lane] = S.X[0][lane][2] - aphi * S.X[0][lane][1];
+        const ff zero = ff_make(0.0f);
+        const ff xx = lane < n ? S.X[0][lane][2] : zero;
+        const ff aphi = ff_div(ff_warp_sum(xx), svs);
+        if (lane < n) abar[lane] = ff_sub(xx, ff_mul(aphi, S.X[0][lane][1]));
     }
     __syncthreads();
     // dL/dtheta_p = sum_i abar_i (dc0_i/dtheta_p - sum_j d(A+B)_ij/dtheta_p w_j), i, j over the points
     // eight threads per point i, each over every eighth j
-    double tp3[3] = {0.0, 0.0, 0.0};
+    ff tp3[3] = {ff_make(0.0f), ff_make(0.0f), ff_make(0.0f)};
     {
         const int i = tid >> 3, q = tid & 7;
         if (i < n) {
             const int dxi = S.dx[i], dyi = S.dy[i];
             const int i0 = abs(dyi) * nr + abs(dxi);
-            double acc[3] = {0.0, 0.0, 0.0};
-            if (q == 0)
+            ff acc[3] = {ff_make(0.0f), ff_make(0.0f), ff_make(0.0f)};
+            if (q == 0) {
+#pragma unroll
                 for (int p = 0; p < 3; ++p) acc[p] = d0[p][i0];
+            }
             for (int j = q; j < n; j += 8) {
                 const int ic = abs(dyi - S.dy[j]) * n2r + abs(dxi - S.dx[j]);
-                for (int p = 0; p < 3; ++p) acc[p] -= (dC[p][ic] + dC[p][nn + ic]) * wgt[j];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) acc[p] = ff_sub(acc[p], ff_mul(ff_add(dC[p][ic], dC[p][nn + ic]), wgt[j]));
             }
-            for (int p = 0; p < 3; ++p) tp3[p] = abar[i] * acc[p];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) tp3[p] = ff_mul(abar[i], acc[p]);
         }
     }
-    for (int p = 0; p < 3; ++p)
-        for (int o = 16; o; o >>= 1) tp3[p] += __shfl_xor_sync(0xffffffffu, tp3[p], o);
-    if (lane == 0)
+#pragma unroll
+    for (int p = 0; p < 3; ++p) tp3[p] = ff_warp_sum(tp3[p]);
+    if (lane == 0) {
+#pragma unroll
         for (int p = 0; p < 3; ++p) red[warp][p] = tp3[p];
+    }
     __syncthreads();
     if (tid < 3) {
-        double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w][tid];
-        atomicAdd(P.grad_params + 3 * v + tid, s);
+        ff s = red[0][tid];
+        for (int w = 1; w < 8; ++w) s = ff_add(s, red[w][tid]);
+        atomicAdd(P.grad_params + 3 * v + tid, ff_to_double(s));
     }
 }
 
