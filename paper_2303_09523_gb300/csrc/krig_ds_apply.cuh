@@ -30,11 +30,24 @@
 #include "krig_device.cuh"
 
 template <typename TI> struct DsTypes;
-template <> struct DsTypes<double> { typedef double TC; typedef double TO; static constexpr int PAD = 4, RP = 72; };
-template <> struct DsTypes<float> { typedef float TC; typedef float TO; static constexpr int PAD = 8, RP = 80; };
-template <> struct DsTypes<uint16_t> { typedef float TC; typedef float TO; static constexpr int PAD = 8, RP = 96; };
-// RP (elements per shared row) >= TX + 2 PAD; RP * sizeof is 64 mod 128 bytes so the
-// two rows read by a quarter warp fall in different banks.
+template <> struct DsTypes<double> {
+    typedef double TC, TO, TW;
+    static constexpr int PAD = 4, RP = 72;
+};
+template <> struct DsTypes<float> {
+    typedef float TC, TO;
+    typedef unsigned long long TW;
+    static constexpr int PAD = 8, RP = 80;
+};
+template <> struct DsTypes<uint16_t> {
+    typedef float TC, TO;
+    typedef unsigned long long TW;
+    static constexpr int PAD = 8, RP = 96;
+};
+// TC: arithmetic type; TO: output type; TW: orbit-weight entry in shared memory
+// (FP32: the weight twice, the operand of the packed FMAs).  RP (elements per
+// shared row) >= TX + 2 PAD; RP * sizeof is 64 mod 128 bytes so the two rows
+// read by a quarter warp fall in different banks.
 
 #define DS_CONSUMERS 8                      // consumer warps (tiles)
 #define DS_PRODUCER DS_CONSUMERS            // streams the known-slice tiles
@@ -322,24 +335,19 @@ template <typename TI> struct DsLayout {
     static constexpr size_t bar_off = (size_t)S * stride * sizeof(TI);
     static constexpr size_t flag_off = bar_off + (2 * S + 1) * sizeof(uint64_t);
     static constexpr size_t ow_off = (flag_off + 4 * (1 + DS_CONSUMERS) + 15) / 16 * 16;
-    static constexpr size_t ow_per_vol = 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(TC);
+    static constexpr size_t ow_per_vol = 2 * KRIG_NORB * KRIG_TSLOTS * sizeof(typename DsTypes<TI>::TW);
     __host__ __device__ static constexpr size_t vol_off(int nv) { return ow_off + (size_t)nv * ow_per_vol; }
-    // per consumer thread, the orbit sums of the previous slice when they do not stay in
-    // registers (ds_lo_smem): [NORB][256 threads][4 pixels]
-    __host__ __device__ static constexpr size_t orb_off(int nv)
-    {
-        return (vol_off(nv) + (size_t)nv * sizeof(DsVolS) + 15) / 16 * 16;
-    }
-    static constexpr size_t orb_bytes = (size_t)KRIG_NORB * DS_CONSUMERS * 32 * KRIG_PX * sizeof(TC);
-    __host__ __device__ static constexpr size_t bytes(int nv) { return orb_off(nv) + orb_bytes; }
-    __device__ static __forceinline__ TC* orb(int nv) { return (TC*)(ds_smem + orb_off(nv)); }
+    __host__ __device__ static constexpr size_t bytes(int nv) { return vol_off(nv) + (size_t)nv * sizeof(DsVolS); }
     __device__ static __forceinline__ TI* slots() { return (TI*)ds_smem; }
     __device__ static __forceinline__ uint64_t* full() { return (uint64_t*)(ds_smem + bar_off); }
     __device__ static __forceinline__ uint64_t* empty() { return (uint64_t*)(ds_smem + bar_off) + S; }
     __device__ static __forceinline__ uint64_t* never() { return (uint64_t*)(ds_smem + bar_off) + 2 * S; }
     __device__ static __forceinline__ int* abort_flag() { return (int*)(ds_smem + flag_off); }
     __device__ static __forceinline__ int* pending(int warp) { return (int*)(ds_smem + flag_off) + 1 + warp; }
-    __device__ static __forceinline__ TC* ow() { return (TC*)(ds_smem + ow_off); }
+    __device__ static __forceinline__ typename DsTypes<TI>::TW* ow()
+    {
+        return (typename DsTypes<TI>::TW*)(ds_smem + ow_off);
+    }
     __device__ static __forceinline__ const DsVolS* vols(int nv) { return (const DsVolS*)(ds_smem + vol_off(nv)); }
 };
 
@@ -387,10 +395,18 @@ __device__ __forceinline__ int ds_first_item(int lo)
 }
 
 // ---------------------------------------------------------------------------
-// Interior path: D4 orbit sums of one known slice around the thread's four
-// pixels (orbits {same max(|dx|,|dy|), min(|dx|,|dy|)}: 1, 3, 6 for r = 0, 1, 2),
-// computed once per slice and kept in registers for both gaps the slice
-// brackets; then one weight per orbit and target.
+// Interior path.  A thread owns four consecutive pixels, taken as two pixel
+// pairs; every orbit sum, partial sum and output of a pair is one packed value
+// (FP32: a 64-bit register pair and the f32x2 instructions, each half rounding
+// as the scalar instruction; FP64: two doubles), so the arithmetic needs no
+// operand shuffling.  The D4 orbit sums of a known slice ({same
+// max(|dx|,|dy|), min(|dx|,|dy|)}: 1, 3, 6 for r = 0, 1, 2) are formed once per
+// slice.  The slice then completes the gap below it as its upper slice, from
+// the partial sums over the lower slice kept since that one arrived, and
+// starts the gap above it as its lower slice (new partial sums); between
+// slices a thread keeps g - 1 partial sums per pixel pair, not a slice of
+// orbit sums.  Every output is sum_s sum_o w[s][o][t] O_s[o] accumulated in
+// the order s = lower, upper and o ascending, by fused multiply-adds.
 // ---------------------------------------------------------------------------
 // Two floats as one 64-bit register pair and back (operands of the packed
 // f32x2 instructions).
@@ -406,138 +422,115 @@ __device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b)
 }
 
 template <int R> struct DsNO { static constexpr int N = R == 0 ? 1 : (R == 1 ? 3 : 6); };
-template <int GM1> struct DsGP { static constexpr int N = GM1 > 0 ? GM1 : 1; };  // accumulators per pixel
+template <int GM1> struct DsGP { static constexpr int N = GM1 > 0 ? GM1 : 1; };  // partial sums per pixel pair
 
+// One quantity at two adjacent pixels.
+template <typename TC> struct Px2;
+template <> struct Px2<float> {
+    unsigned long long v;
+    __device__ __forceinline__ static Px2 of(float a, float b) { return {pk2(a, b)}; }
+    __device__ __forceinline__ static Px2 zero() { return {0ull}; }
+    __device__ __forceinline__ float x() const { float a, b; upk2(v, a, b); return a; }
+    __device__ __forceinline__ float y() const { float a, b; upk2(v, a, b); return b; }
+};
+template <> struct Px2<double> {
+    double a, b;
+    __device__ __forceinline__ static Px2 of(double x, double y) { return {x, y}; }
+    __device__ __forceinline__ static Px2 zero() { return {0.0, 0.0}; }
+    __device__ __forceinline__ double x() const { return a; }
+    __device__ __forceinline__ double y() const { return b; }
+};
+__device__ __forceinline__ Px2<float> operator+(Px2<float> p, Px2<float> q)
+{
+    Px2<float> r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(p.v), "l"(q.v));
+    return r;
+}
+__device__ __forceinline__ Px2<double> operator+(Px2<double> p, Px2<double> q) { return {p.a + q.a, p.b + q.b}; }
+// acc += w * z, half by half
+__device__ __forceinline__ void px_fma(Px2<float>& acc, Px2<float> w, Px2<float> z)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc.v) : "l"(w.v), "l"(z.v));
+}
+__device__ __forceinline__ void px_fma(Px2<double>& acc, Px2<double> w, Px2<double> z)
+{
+    acc.a = fma(w.a, z.a, acc.a);
+    acc.b = fma(w.b, z.b, acc.b);
+}
+// A weight of the shared-memory table as the pair (w, w): FP32 tables hold the
+// pair already, FP64 tables the value.
+__device__ __forceinline__ Px2<float> px_w(unsigned long long w) { return {w}; }
+__device__ __forceinline__ Px2<double> px_w(double w) { return {w, w}; }
+
+// One shared row around the thread's pixels: columns lcol-4 .. lcol+7 (pixel
+// p at column 4 + p) as six column pairs; only the pairs a window of half
+// width R reaches are loaded.
+template <typename TI, int R>
+__device__ __forceinline__ void ds_row_pairs(const TI* rowp, Px2<typename DsTypes<TI>::TC> (&c)[6])
+{
+    typedef typename DsTypes<TI>::TC TC;
+    TC v[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[i] = TC(0);
+    if (R > 0) ld4(rowp - 4, v);
+    ld4(rowp, v + 4);
+    if (R > 0) ld4(rowp + 4, v + 8);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c[i] = Px2<TC>::of(v[2 * i], v[2 * i + 1]);
+}
+
+// Pixel pair k (columns m = 4 + 2k, m + 1) of a row of pairs: the values
+// themselves, c[m - 1] + c[m + 1] (shift 1) and c[m - 2] + c[m + 2] (shift 2).
+template <typename TC>
+__device__ __forceinline__ Px2<TC> px_s1(const Px2<TC> (&c)[6], int k)
+{
+    const int h = 2 + k;  // pair index of column m
+    return Px2<TC>::of(c[h - 1].y() + c[h].y(), c[h].x() + c[h + 1].x());
+}
+template <typename TC>
+__device__ __forceinline__ Px2<TC> px_s2(const Px2<TC> (&c)[6], int k)
+{
+    return c[1 + k] + c[3 + k];
+}
+
+// D4 orbit sums of one known slice at the thread's two pixel pairs:
+//   o0 = c, o1 = (c(+-1, 0)) + (c(0, +-1)), o2 = c(+-1, +-1),
+//   o3 = (c(+-2, 0)) + (c(0, +-2)), o4 = (c(+-2, +-1)) + (c(+-1, +-2)), o5 = c(+-2, +-2),
+// with each parenthesised pair of taps added first, rows +-d summed before the
+// column shifts.
 template <typename TI, int R>
 __device__ __forceinline__ void ds_orbits(const TI* slot, int lrow, int lcol,
-                                          typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
+                                          Px2<typename DsTypes<TI>::TC> (&O)[2][DsNO<R>::N])
 {
     typedef typename DsTypes<TI>::TC TC;
     constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    // columns 4-R .. 7+R of the 12 loaded around the thread's four pixels
-    TC c0[12], a1[12], a2[12];
-    {
-        const TI* rowp = slot + (lrow + R) * RP + PAD + lcol;
-        TC a[4], b[4], c[4];
-        if (R > 0) ld4(rowp - 4, a);
-        ld4(rowp, b);
-        if (R > 0) ld4(rowp + 4, c);
+    const TI* base = slot + (lrow + R) * RP + PAD + lcol;
+    Px2<TC> c0[6];
+    ds_row_pairs<TI, R>(base, c0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            c0[q] = R > 0 ? a[q] : TC(0);
-            c0[4 + q] = b[q];
-            c0[8 + q] = R > 0 ? c[q] : TC(0);
-        }
-    }
+    for (int k = 0; k < 2; ++k) O[k][0] = c0[2 + k];
     if (R >= 1) {
-        const TI* rm = slot + (lrow + R - 1) * RP + PAD + lcol;
-        const TI* rp = slot + (lrow + R + 1) * RP + PAD + lcol;
-        TC a[4], b[4], c[4], d[4], e[4], f[4];
-        ld4(rm - 4, a);
-        ld4(rm, b);
-        ld4(rm + 4, c);
-        ld4(rp - 4, d);
-        ld4(rp, e);
-        ld4(rp + 4, f);
+        Px2<TC> a1[6], b[6];
+        ds_row_pairs<TI, R>(base - RP, a1);
+        ds_row_pairs<TI, R>(base + RP, b);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a1[q] = a[q] + d[q];
-            a1[4 + q] = b[q] + e[q];
-            a1[8 + q] = c[q] + f[q];
-        }
-    }
-    if (R >= 2) {
-        const TI* rm = slot + (lrow + R - 2) * RP + PAD + lcol;
-        const TI* rp = slot + (lrow + R + 2) * RP + PAD + lcol;
-        TC a[4], b[4], c[4], d[4], e[4], f[4];
-        ld4(rm - 4, a);
-        ld4(rm, b);
-        ld4(rm + 4, c);
-        ld4(rp - 4, d);
-        ld4(rp, e);
-        ld4(rp + 4, f);
+        for (int i = 0; i < 6; ++i) a1[i] = a1[i] + b[i];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a2[q] = a[q] + d[q];
-            a2[4 + q] = b[q] + e[q];
-            a2[8 + q] = c[q] + f[q];
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < KRIG_PX; ++p) {
-        const int m = 4 + p;  // centre column
-        orb[p][0] = c0[m];
-        if (R >= 1) {
-            orb[p][1] = (c0[m - 1] + c0[m + 1]) + a1[m];
-            orb[p][2] = a1[m - 1] + a1[m + 1];
+        for (int k = 0; k < 2; ++k) {
+            O[k][1] = px_s1(c0, k) + a1[2 + k];
+            O[k][2] = px_s1(a1, k);
         }
         if (R >= 2) {
-            orb[p][3] = (c0[m - 2] + c0[m + 2]) + a2[m];
-            orb[p][4] = (a1[m - 2] + a1[m + 2]) + (a2[m - 1] + a2[m + 1]);
-            orb[p][5] = a2[m - 2] + a2[m + 2];
-        }
-    }
-}
-
-// The thread's four pixel values of one known slice (the orbit-0 sums).
-template <typename TI, int R>
-__device__ __forceinline__ void ds_centres(const TI* slot, int lrow, int lcol,
-                                           typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
-{
-    typedef typename DsTypes<TI>::TC TC;
-    constexpr int PAD = DsTypes<TI>::PAD, RP = DsTypes<TI>::RP;
-    TC b[4];
-    ld4(slot + (lrow + R) * RP + PAD + lcol, b);
+            Px2<TC> a2[6];
+            ds_row_pairs<TI, R>(base - 2 * RP, a2);
+            ds_row_pairs<TI, R>(base + 2 * RP, b);
 #pragma unroll
-    for (int p = 0; p < KRIG_PX; ++p) {
-        orb[p][0] = b[p];
+            for (int i = 0; i < 6; ++i) a2[i] = a2[i] + b[i];
 #pragma unroll
-        for (int o = 1; o < DsNO<R>::N; ++o) orb[p][o] = TC(0);
-    }
-}
-
-// Targets t0 and t0 + 1 (t0 + 1 < GM1 or not) of the four pixels from the orbit
-// sums of both slices: acc[p][i] = sum_o wl[o][t0+i] lo[p][o] + wh[o][t0+i] hi[p][o];
-// ow: the item's [2][NORB][8] orbit weights in shared memory.  One target pair
-// at a time keeps few accumulators live beside the two slices' orbit sums.
-template <typename TI, int R, int GM1>
-__device__ __forceinline__ void ds_fma_pair(typename DsTypes<TI>::TC (&acc)[KRIG_PX][2], int t0,
-                                            const typename DsTypes<TI>::TC (&lo)[KRIG_PX][DsNO<R>::N],
-                                            const typename DsTypes<TI>::TC (&hi)[KRIG_PX][DsNO<R>::N],
-                                            const typename DsTypes<TI>::TC* ow)
-{
-    typedef typename DsTypes<TI>::TC TC;
-    const bool two = t0 + 1 < GM1;
-#pragma unroll
-    for (int p = 0; p < KRIG_PX; ++p) acc[p][0] = acc[p][1] = TC(0);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-#pragma unroll
-        for (int o = 0; o < DsNO<R>::N; ++o) {
-            const TC* wp = ow + (s * KRIG_NORB + o) * KRIG_TSLOTS + t0;
-            if constexpr (sizeof(TC) == 4) {
-                // two targets per packed FMA (fma.rn.f32x2: each half rounds as fmaf)
-                const float2 w = *(const float2*)wp;
-                const unsigned long long wpk = pk2(w.x, w.y);
-#pragma unroll
-                for (int p = 0; p < KRIG_PX; ++p) {
-                    const TC z = s == 0 ? lo[p][o] : hi[p][o];
-                    if (two) {
-                        unsigned long long a2 = pk2(acc[p][0], acc[p][1]);
-                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(wpk), "l"(pk2(z, z)));
-                        upk2(a2, acc[p][0], acc[p][1]);
-                    } else {
-                        acc[p][0] = fmaf(w.x, z, acc[p][0]);
-                    }
-                }
-            } else {
-                const double2 w = *(const double2*)wp;
-#pragma unroll
-                for (int p = 0; p < KRIG_PX; ++p) {
-                    const TC z = s == 0 ? lo[p][o] : hi[p][o];
-                    acc[p][0] = fma(w.x, z, acc[p][0]);
-                    if (two) acc[p][1] = fma(w.y, z, acc[p][1]);
-                }
+            for (int k = 0; k < 2; ++k) {
+                O[k][3] = px_s2(c0, k) + a2[2 + k];
+                O[k][4] = px_s2(a1, k) + px_s1(a2, k);
+                O[k][5] = px_s2(a2, k);
             }
         }
     }
@@ -592,15 +585,18 @@ __device__ __forceinline__ DsCtx<TI> ds_ctx(const DsVolS& V, const unsigned char
     return c;
 }
 
-// Known slice -> its output slice, bit-exact (u16: float32(u) * scale).
-template <typename TI, int R>
-__device__ __forceinline__ void ds_passthrough(const DsCtx<TI>& c, int64_t off,
-                                               const typename DsTypes<TI>::TC (&orb)[KRIG_PX][DsNO<R>::N])
+// Known slice -> its output slice, bit-exact (u16: float32(u) * scale); o: the
+// slice's values at the two pixel pairs.
+template <typename TI>
+__device__ __forceinline__ void ds_passthrough(const DsCtx<TI>& c, int64_t off, Px2<typename DsTypes<TI>::TC> o0,
+                                               Px2<typename DsTypes<TI>::TC> o1)
 {
     typedef typename DsTypes<TI>::TO TO;
-    TO kv[4];
+    TO kv[4] = {(TO)o0.x(), (TO)o0.y(), (TO)o1.x(), (TO)o1.y()};
+    if (sizeof(TI) == 2) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) kv[p] = sizeof(TI) == 2 ? (TO)__fmul_rn((float)orb[p][0], c.scale) : (TO)orb[p][0];
+        for (int p = 0; p < 4; ++p) kv[p] = (TO)__fmul_rn((float)kv[p], c.scale);
+    }
     st4<TO>(c.out + off, kv, c.vec_out, c.nvalid);
     if (c.var) {
         const float z4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -608,26 +604,65 @@ __device__ __forceinline__ void ds_passthrough(const DsCtx<TI>& c, int64_t off,
     }
 }
 
-// Interpolated output slice t (1 <= t < g) of gap j for the interior pixels of
-// the four (and their kriging variance).
+// acc[t][k] += sum_o w[o][t] O[k][o] for every target t (o ascending): w is one
+// slice's [NORB][8] block of the orbit-weight table; the FP32 table is read two
+// targets ((w_t, w_t), (w_t+1, w_t+1)) per 16-byte load.
+template <typename TI, int NO, int GM1>
+__device__ __forceinline__ void ds_accum_slice(Px2<typename DsTypes<TI>::TC> (&acc)[DsGP<GM1>::N][2],
+                                               const Px2<typename DsTypes<TI>::TC> (&O)[2][NO],
+                                               const typename DsTypes<TI>::TW* w)
+{
+    typedef typename DsTypes<TI>::TC TC;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+#pragma unroll
+        for (int t = 0; t < GM1; t += 2) {
+            Px2<TC> wa, wb;
+            if constexpr (sizeof(TC) == 4) {
+                const ulonglong2 q = *(const ulonglong2*)(w + o * KRIG_TSLOTS + t);
+                wa = px_w(q.x);
+                wb = px_w(q.y);
+            } else {
+                const double2 q = *(const double2*)(w + o * KRIG_TSLOTS + t);
+                wa = px_w(q.x);
+                wb = px_w(q.y);
+            }
+            px_fma(acc[t][0], wa, O[0][o]);
+            px_fma(acc[t][1], wa, O[1][o]);
+            if (t + 1 < GM1) {
+                px_fma(acc[t + 1][0], wb, O[0][o]);
+                px_fma(acc[t + 1][1], wb, O[1][o]);
+            }
+        }
+    }
+}
+
+// Interpolated output slice (target t + 1) at offset off for the interior
+// pixels of the four (and their kriging variance); u0, u1: the two pixel pairs.
 template <typename TI>
-__device__ __forceinline__ void ds_store_t(const DsCtx<TI>& c, int64_t jg, int t, const typename DsTypes<TI>::TC (&acc)[KRIG_PX][2],
-                                           int i)
+__device__ __forceinline__ void ds_store_t(const DsCtx<TI>& c, int64_t off, int t, Px2<typename DsTypes<TI>::TC> u0,
+                                           Px2<typename DsTypes<TI>::TC> u1)
 {
     typedef typename DsTypes<TI>::TO TO;
-    const int64_t off = jg + (int64_t)t * c.plane;
+    typedef typename DsTypes<TI>::TC TC;
+    TC v[4] = {u0.x(), u0.y(), u1.x(), u1.y()};
+    if (c.clamp) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)  // comparisons keep a NaN (singular system) a NaN
+            v[p] = v[p] < c.lo ? c.lo : (v[p] > c.hi ? c.hi : v[p]);
+    }
     if (c.full) {
         TO o[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) o[p] = (TO)acc[p][i];
+        for (int p = 0; p < 4; ++p) o[p] = (TO)v[p];
         st4<TO>(c.out + off, o, true, 4);
     } else {
 #pragma unroll
         for (int p = 0; p < 4; ++p)
-            if (p >= c.plo && p < c.phi) c.out[off + p] = (TO)acc[p][i];
+            if (p >= c.plo && p < c.phi) c.out[off + p] = (TO)v[p];
     }
     if (c.var) {
-        const float vv = c.vt[t - 1];
+        const float vv = c.vt[t];
         if (c.full) {
             const float v4[4] = {vv, vv, vv, vv};
             st4<float>(c.var + off, v4, true, 4);
@@ -638,113 +673,60 @@ __device__ __forceinline__ void ds_store_t(const DsCtx<TI>& c, int64_t jg, int t
 }
 
 // One item for one consumer warp: its 8 x 16 pixel block of the tile, every
-// gap of the item's chunk.  Each known slice's orbit sums are computed once,
-// right after its slot fills, and the slot is released at once (the sums stay
-// in registers for the next gap).  dry: warm-up pass over the first gap, no
-// stores and no release (the slots stay full for the real pass).  Returns
-// false if a wait gave up.
-// Where the previous slice's orbit sums wait for the next gap: in registers,
-// or, for the larger windows (r = 2; r >= 1 in FP64), in the thread's own
-// shared-memory rows, so that they are not live while the next slice's sums are
-// formed (the consumer code is held to 96 registers).
-template <typename TI, int R> struct DsLoSmem { static constexpr bool V = R == 2 || (sizeof(TI) == 8 && R >= 1); };
-
-template <typename TC, int NO>
-__device__ __forceinline__ void ds_put_orbits(TC* base, const TC (&o)[KRIG_PX][NO])
-{
-#pragma unroll
-    for (int k = 0; k < NO; ++k) {
-        TC* p = base + (size_t)k * (DS_CONSUMERS * 32 * KRIG_PX);
-        if constexpr (sizeof(TC) == 4) {
-            *(float4*)p = make_float4(o[0][k], o[1][k], o[2][k], o[3][k]);
-        } else {
-            *(double2*)p = make_double2(o[0][k], o[1][k]);
-            *(double2*)(p + 2) = make_double2(o[2][k], o[3][k]);
-        }
-    }
-}
-
-template <typename TC, int NO>
-__device__ __forceinline__ void ds_get_orbits(const TC* base, TC (&o)[KRIG_PX][NO])
-{
-#pragma unroll
-    for (int k = 0; k < NO; ++k) {
-        TC v[4];
-        ld4(base + (size_t)k * (DS_CONSUMERS * 32 * KRIG_PX), v);
-#pragma unroll
-        for (int p = 0; p < KRIG_PX; ++p) o[p][k] = v[p];
-    }
-}
-
-// One item for one consumer warp: its 8 x 16 pixel block of the tile, every
-// gap of the item's chunk.  Each known slice's orbit sums are computed once,
-// right after its slot fills, and the slot is released at once (the sums are
-// kept for the next gap).  dry: warm-up pass over the first gap, no stores and
-// no release (the slots stay full for the real pass).  Returns false if a wait
-// gave up.
+// gap of the item's chunk.  Each known slice's orbit sums are formed right
+// after its slot fills, and the slot is released at once.  dry: warm-up pass
+// over the first gap while the class solve may still run, with no release
+// (the slots stay full for the real pass); its stores, from weights not yet
+// final, go to the same addresses as the real pass's, which follows in the
+// same thread and overwrites them.  ow: the volume's orbit-weight table
+// [2][NORB][8] in shared memory.  Returns false if a wait gave up.
 template <typename TI, int R, int GM1>
 __device__ __forceinline__ bool ds_item(const DsCtx<TI>& c, const DsItem& d, int q, int lrow, int lcol, int lane,
-                                        const typename DsTypes<TI>::TC* ow, int nv, bool dry)
+                                        const typename DsTypes<TI>::TW* ow, bool dry)
 {
     typedef typename DsTypes<TI>::TC TC;
     constexpr int S = DsStages<TI>::S;
     constexpr int NO = DsNO<R>::N;
-    constexpr bool LS = DsLoSmem<TI, R>::V;
+    constexpr int GP = DsGP<GM1>::N;
     TI* slots = DsLayout<TI>::slots();
     uint64_t* full = DsLayout<TI>::full();
     uint64_t* empty = DsLayout<TI>::empty();
     constexpr int stride = DsLayout<TI>::stride;
-    TC* lsm = DsLayout<TI>::orb(nv) + threadIdx.x * KRIG_PX;  // this thread's rows (consumers: tid < 256)
     const int nsl = dry ? 2 : d.c1 - d.c0 + 1;  // warm-up: the first gap only
-    const bool orbits = GM1 > 0 && c.inner;
-    TC lo[KRIG_PX][NO];
-    if (!mbar_wait(&full[q % S], (q / S) & 1, DS_WAIT_LIMIT)) return false;
-    if (orbits) ds_orbits<TI, R>(slots + (q % S) * stride, lrow, lcol, lo);
-    else ds_centres<TI, R>(slots + (q % S) * stride, lrow, lcol, lo);
-    __syncwarp();
-    if (lane == 0 && !dry) mbar_arrive(&empty[q % S]);
-    if (LS) ds_put_orbits<TC, NO>(lsm, lo);
-    for (int m = 0; m + 1 < nsl; ++m) {
-        const int j = d.c0 + m, qh = q + m + 1;
-        const int64_t jg = (int64_t)j * c.g * c.plane;
-        TC hi[KRIG_PX][NO];
-        if (!mbar_wait(&full[qh % S], (qh / S) & 1, DS_WAIT_LIMIT)) return false;
-        if (orbits) ds_orbits<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
-        else ds_centres<TI, R>(slots + (qh % S) * stride, lrow, lcol, hi);
+    const bool fma_px = GM1 > 0 && c.inner;
+    // partial sums over the lower slice of the current gap (defined from the
+    // start: a conditionally assigned array is kept in local memory)
+    Px2<TC> L[GP][2];
+#pragma unroll
+    for (int t = 0; t < GP; ++t) L[t][0] = L[t][1] = Px2<TC>::zero();
+    for (int m = 0; m < nsl; ++m) {
+        const int j = d.c0 + m, qs = q + m;  // slice j
+        if (!mbar_wait(&full[qs % S], (qs / S) & 1, DS_WAIT_LIMIT)) return false;
+        Px2<TC> O[2][NO];
+        ds_orbits<TI, R>(slots + (qs % S) * stride, lrow, lcol, O);
         __syncwarp();
-        if (lane == 0 && !dry) mbar_arrive(&empty[qh % S]);
-        if (LS) ds_get_orbits<TC, NO>(lsm, lo);
-        if (c.mine && !dry) ds_passthrough<TI, R>(c, jg, lo);
+        if (lane == 0 && !dry) mbar_arrive(&empty[qs % S]);
+        const int64_t jg = (int64_t)j * c.g * c.plane;  // output offset of slice j
+        // slices c0 .. c1-1 are the lower slices of this item's gaps; the last
+        // slice of the volume is passed through by the item of the last gap
+        if (c.mine && (m + 1 < nsl || j - 1 == c.jlast)) ds_passthrough<TI>(c, jg, O[0][0], O[1][0]);
         if constexpr (GM1 > 0) {
-            if (orbits) {
-                // one target pair at a time: the accumulators and weights of one
-                // pair live beside the two slices' orbit sums
+            if (fma_px) {
+                if (m > 0) {
+                    // upper slice of gap j - 1: complete its targets in place (the
+                    // chains of all targets are independent), then store them
+                    ds_accum_slice<TI, NO, GM1>(L, O, ow + KRIG_NORB * KRIG_TSLOTS);
+                    int64_t off = jg - (int64_t)(c.g - 1) * c.plane;  // target 1 of gap j - 1
 #pragma unroll
-                for (int t0 = 0; t0 < GM1; t0 += 2) {
-                    TC acc[KRIG_PX][2];
-                    ds_fma_pair<TI, R, GM1>(acc, t0, lo, hi, ow);
-                    if (c.clamp) {
+                    for (int t = 0; t < GM1; ++t, off += c.plane) ds_store_t<TI>(c, off, t, L[t][0], L[t][1]);
+                }
+                if (m + 1 < nsl) {
+                    // lower slice of gap j: its partial sums
 #pragma unroll
-                        for (int p = 0; p < KRIG_PX; ++p)
-#pragma unroll
-                            for (int i = 0; i < 2; ++i)  // comparisons keep a NaN (singular system) a NaN
-                                acc[p][i] = acc[p][i] < c.lo ? c.lo : (acc[p][i] > c.hi ? c.hi : acc[p][i]);
-                    }
-                    if (!dry) {
-                        ds_store_t<TI>(c, jg, t0 + 1, acc, 0);
-                        if (t0 + 1 < GM1) ds_store_t<TI>(c, jg, t0 + 2, acc, 1);
-                    }
+                    for (int t = 0; t < GM1; ++t) L[t][0] = L[t][1] = Px2<TC>::zero();
+                    ds_accum_slice<TI, NO, GM1>(L, O, ow);
                 }
             }
-        }
-        if (j == c.jlast && c.mine && !dry) ds_passthrough<TI, R>(c, jg + (int64_t)c.g * c.plane, hi);
-        if (LS) {
-            ds_put_orbits<TC, NO>(lsm, hi);
-        } else {
-#pragma unroll
-            for (int p = 0; p < KRIG_PX; ++p)
-#pragma unroll
-                for (int o = 0; o < NO; ++o) lo[p][o] = hi[p][o];
         }
     }
     return true;
@@ -760,12 +742,14 @@ __device__ __noinline__ void ds_weights_ready(const unsigned char* ws, int nv, i
 {
     typedef typename DsTypes<TI>::TC TC;
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    TC* owsm = DsLayout<TI>::ow();
+    typename DsTypes<TI>::TW* owsm = DsLayout<TI>::ow();
     const DsVolS* tab = DsLayout<TI>::vols(nv);
     constexpr int NW = 2 * KRIG_NORB * KRIG_TSLOTS;
     for (int e = threadIdx.x; e < nv * NW; e += DS_CONSUMERS * 32) {
         const DsVolS& Vv = tab[e / NW];
-        owsm[e] = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(ws + Vv.otab_off))[e % NW] : TC(0);
+        const TC w = (Vv.dtype == dtype && Vv.cint >= 0) ? ((const TC*)(ws + Vv.otab_off))[e % NW] : TC(0);
+        if constexpr (sizeof(TC) == 4) owsm[e] = pk2(w, w);
+        else owsm[e] = w;
     }
     asm volatile("bar.sync 1, %0;" ::"n"(DS_CONSUMERS * 32) : "memory");
 }
@@ -798,7 +782,7 @@ __device__ __noinline__ int ds_run_shape(const DsRunArgs a, const int8_t* order,
         DsItem d;
         if (!ds_decode(V, it, d)) continue;
         if (*(volatile int*)DsLayout<TI>::abort_flag()) return -1;
-        const TC* ow = DsLayout<TI>::ow() + v * (2 * KRIG_NORB * KRIG_TSLOTS);
+        const typename DsTypes<TI>::TW* ow = DsLayout<TI>::ow() + v * (2 * KRIG_NORB * KRIG_TSLOTS);
         // First item of the warp: a warm-up pass over its first gap (the same code,
         // no stores) while the class solve may still run, so the consumer code is
         // cached when the weights arrive; only then the wait (ds_weights_ready).
@@ -809,7 +793,7 @@ __device__ __noinline__ int ds_run_shape(const DsRunArgs a, const int8_t* order,
                 *pending = 0;
             }
             const DsCtx<TI> c = ds_ctx<TI, R>(V, a.ws, d, lrow, lcol, dry);
-            if (!ds_item<TI, R, GM1>(c, d, q, lrow, lcol, a.lane, ow, a.nv, dry)) return -1;
+            if (!ds_item<TI, R, GM1>(c, d, q, lrow, lcol, a.lane, ow, dry)) return -1;
         }
         q += d.c1 - d.c0 + 1;
     }
