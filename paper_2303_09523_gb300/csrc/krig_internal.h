@@ -252,6 +252,9 @@ inline void krig_fill_vol(KrigVol& V, const krig_volume_desc& d, int form, int c
 // KRIG_LOO_REP copies (block index modulo KRIG_LOO_REP), so that no address
 // takes more than a few dozen atomic adds; the readers sum the copies.
 #define KRIG_LOO_REP 32
+// Target slices per residual work item: an item walks a chain of consecutive
+// targets of one tile, so each slice of the chain is read once.
+#define KRIG_LOO_CHAIN 8
 inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* items, int64_t* adj)
 {
     const auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
@@ -261,7 +264,7 @@ inline void krig_fill_loo(KrigVol& V, int64_t* off, int64_t* classes, int64_t* i
     V.loo_cls_begin = *classes;
     *classes += ncls;
     V.loo_item_begin = *items;
-    *items += (int64_t)(V.n - 2) * tiles;
+    *items += (int64_t)((V.n - 2 + KRIG_LOO_CHAIN - 1) / KRIG_LOO_CHAIN) * tiles;
     V.loo_adj_begin = *adj;
     *adj += (int64_t)V.n * tiles;
     V.lw_off = *off;

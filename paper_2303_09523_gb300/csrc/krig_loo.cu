@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "krig_device.cuh"
 
 #define LOO_TX 64
@@ -504,120 +506,145 @@ __device__ __forceinline__ void loo_orbits(const float* a, const float* b, int l
     }
 }
 
+// One chain item: targets j in [ja, jb) of the tile at (x0, y0).  Four slice
+// buffers (tile plus halo) rotate in shared memory: target j reads j - 1, j and
+// j + 1; slice j + 2, loaded into registers during the previous step, is
+// stored after it, while the loads of slice j + 3 are in flight, so each slice
+// of the chain is read once and a load has two steps to arrive.  The
+// loss and (mode 1) the interior orbit sums stay in registers over the chain
+// and are reduced once, into copy rep of the accumulators.
 template <int R>
-__device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int y0, int mode, float* sm)
+__device__ void loo_residual_chain(const KrigLaunch& P, int v, int ja, int jb, int x0, int y0, int mode, int rep,
+                                   float* sm)
 {
     constexpr int N2R = 2 * R + 1, NTAP = 2 * N2R * N2R;
     constexpr int ROWS = LOO_TY + 2 * R;
+    constexpr int BUF = ROWS * LOO_SP;
     const KrigVol& V = P.vol[v];
     const int H = V.H, W = V.W;
     const size_t plane = (size_t)H * W;
-    float* lo = sm;
-    float* hi = sm + ROWS * LOO_SP;
-    float* ce = hi + ROWS * LOO_SP;                   // LOO_TY x LOO_TX, target slice
-    float* wsm = ce + LOO_TY * LOO_SP;                // [ncls][NTAP] LOO weights, orbit weights
+    float* wsm = sm + 4 * BUF;                        // [ncls][NTAP] LOO weights, orbit weights
     float* sgo = wsm + loo_wo_off(25 * NTAP) + 8;     // interior sum r * orbit sum (mode 1)
     double* sl = (double*)(sgo + 8);                  // loss partials of the warps (8)
     constexpr int NO = LooNO<R>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncls = V.ncx * V.ncy;
     const float* wo = wsm + loo_wo_off(ncls * NTAP);  // interior weight per orbit
+    const float* lw = wsm;
+    const auto buf = [&](int s) { return sm + (s & 3) * BUF; };
+    const auto fetch = [&](int s, LooStage<ROWS, LOO_RP / 4>& st) {
+        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)s * plane, H, W, y0 - R, x0 - LOO_PAD, st, tid);
+    };
     {
-        LooStage<ROWS, LOO_RP / 4> a, b;
-        LooStage<LOO_TY, LOO_TX / 4> c;
-        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)(j - 1) * plane, H, W, y0 - R, x0 - LOO_PAD, a, tid);
-        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)(j + 1) * plane, H, W, y0 - R, x0 - LOO_PAD, b, tid);
-        loo_fetch(P.in[v], V.dtype, V.scale, (size_t)j * plane, H, W, y0, x0, c, tid);
+        LooStage<ROWS, LOO_RP / 4> a, b, c;
+        fetch(ja - 1, a);
+        fetch(ja, b);
+        fetch(ja + 1, c);
         loo_copy_weights((const float*)(P.ws + V.lw_off), loo_wo_off(ncls * NTAP) + 8, wsm, tid);
-        loo_commit(a, V.scale, lo, tid);
-        loo_commit(b, V.scale, hi, tid);
-        loo_commit(c, V.scale, ce, tid);
+        loo_commit(a, V.scale, buf(ja - 1), tid);
+        loo_commit(b, V.scale, buf(ja), tid);
+        loo_commit(c, V.scale, buf(ja + 1), tid);
         if (tid < 8) sgo[tid] = 0.f;
     }
     __syncthreads();
     const int lrow = (warp >> 2) * 8 + (lane >> 2);
     const int lcol = (warp & 3) * 16 + (lane & 3) * 4;
     const int y = y0 + lrow;
-    const float* lw = wsm;
     float gio[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) gio[o] = 0.f;
-    float loss4 = 0.f;  // the thread's (at most four) squared residuals, FP32
-    float outv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (y < H) {
-        float cev[4];
-        {
-            const float4 c4 = *(const float4*)(ce + lrow * LOO_SP + lcol);
-            cev[0] = c4.x; cev[1] = c4.y; cev[2] = c4.z; cev[3] = c4.w;
-        }
-        // interior pixels: orbit sums of the two slices, one FMA per orbit
-        const bool row_in = V.cint >= 0 && y >= R && y <= H - 1 - R;
-        float orb[4][NO];
-        if (row_in) loo_orbits<R>(lo, hi, lrow, lcol, orb);
-        // residual, loss term and output of pixel p; interior pixels also feed the
-        // orbit sums of dL/dw (border classes: loo_border_block, from the stored residuals)
-        const auto finish = [&](int p, float pred, bool inner) {
-            const float res = pred - cev[p];
-            loss4 = fmaf(res, res, loss4);
-            outv[p] = mode == 0 ? pred : res;
-            if (mode == 1 && inner) {
-#pragma unroll
-                for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
+    double loss = 0.0;
+    const bool row_in = V.cint >= 0 && y >= R && y <= H - 1 - R;
+    const bool all_in = row_in && x0 + lcol >= R && x0 + lcol + 3 <= W - 1 - R;
+    float* dst = mode == 0 ? P.pred[v] : (float*)(P.ws + V.res_off);
+    LooStage<ROWS, LOO_RP / 4> nx, nx2;  // slices j + 2 (loaded) and j + 3 (in flight)
+    if (ja + 2 <= jb) fetch(ja + 2, nx);
+    for (int j = ja; j < jb; ++j) {
+        const bool more = j + 2 <= jb;   // slice j + 2 brackets target j + 1
+        const bool more2 = j + 3 <= jb;
+        if (more2) fetch(j + 3, nx2);
+        const float* lo = buf(j - 1);
+        const float* hi = buf(j + 1);
+        const float* ce = buf(j) + R * LOO_SP + LOO_PAD;  // the target slice, tile rows and columns
+        float loss4 = 0.f;  // the thread's (at most four) squared residuals, FP32
+        float outv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (y < H) {
+            float cev[4];
+            {
+                const float4 c4 = *(const float4*)(ce + lrow * LOO_SP + lcol);
+                cev[0] = c4.x; cev[1] = c4.y; cev[2] = c4.z; cev[3] = c4.w;
             }
-        };
-        if (row_in && x0 + lcol >= R && x0 + lcol + 3 <= W - 1 - R) {
-            // all four pixels in the interior class
+            // interior pixels: orbit sums of the two slices, one FMA per orbit
+            float orb[4][NO];
+            if (row_in) loo_orbits<R>(lo, hi, lrow, lcol, orb);
+            // residual, loss term and output of pixel p; interior pixels also feed the
+            // orbit sums of dL/dw (border classes: loo_border_block, from the stored residuals)
+            const auto finish = [&](int p, float pred, bool inner) {
+                const float res = pred - cev[p];
+                loss4 = fmaf(res, res, loss4);
+                outv[p] = mode == 0 ? pred : res;
+                if (mode == 1 && inner) {
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float pred = 0.f;
+                    for (int o = 0; o < NO; ++o) gio[o] = fmaf(res, orb[p][o], gio[o]);
+                }
+            };
+            if (all_in) {
+                // all four pixels in the interior class
 #pragma unroll
-                for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
-                finish(p, pred, true);
-            }
-        } else {
-            const int cy = V.ymap[krig_slot(y, H, R)];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int x = x0 + lcol + p;
-                if (x >= W) break;
-                const int c = cy * V.ncx + V.xmap[krig_slot(x, W, R)];
-                const bool inner = row_in && c == V.cint;
-                float pred = 0.f;
-                if (inner) {
+                for (int p = 0; p < 4; ++p) {
+                    float pred = 0.f;
 #pragma unroll
                     for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
-                } else {
-                    const float* wr = lw + (int64_t)c * NTAP;
-#pragma unroll
-                    for (int s = 0; s < 2; ++s)
-#pragma unroll
-                        for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                            for (int dx = -R; dx <= R; ++dx) {
-                                const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
-                                pred = fmaf(wr[k], (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_SP + LOO_PAD + lcol + p + dx],
-                                            pred);
-                            }
+                    finish(p, pred, true);
                 }
-                finish(p, pred, inner);
-            }
-        }
-        // predictions (mode 0, when asked for) or residuals (mode 1): one vector store
-        // when the four pixels are in the slice and the row is 16-byte aligned
-        float* dst = mode == 0 ? P.pred[v] : (float*)(P.ws + V.res_off);
-        if (dst) {
-            const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x0 + lcol;
-            if ((W & 3) == 0 && x0 + lcol + 3 < W) {
-                *(float4*)(dst + oidx) = make_float4(outv[0], outv[1], outv[2], outv[3]);
             } else {
+                const int cy = V.ymap[krig_slot(y, H, R)];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    if (x0 + lcol + p < W) dst[oidx + p] = outv[p];
+                for (int p = 0; p < 4; ++p) {
+                    const int x = x0 + lcol + p;
+                    if (x >= W) break;
+                    const int c = cy * V.ncx + V.xmap[krig_slot(x, W, R)];
+                    const bool inner = row_in && c == V.cint;
+                    float pred = 0.f;
+                    if (inner) {
+#pragma unroll
+                        for (int o = 0; o < NO; ++o) pred = fmaf(wo[o], orb[p][o], pred);
+                    } else {
+                        const float* wr = lw + (int64_t)c * NTAP;
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                                for (int dx = -R; dx <= R; ++dx) {
+                                    const int k = (s * N2R + (dy + R)) * N2R + (dx + R);
+                                    pred = fmaf(wr[k],
+                                                (s == 0 ? lo : hi)[(lrow + R + dy) * LOO_SP + LOO_PAD + lcol + p + dx],
+                                                pred);
+                                }
+                    }
+                    finish(p, pred, inner);
+                }
+            }
+            // predictions (mode 0, when asked for) or residuals (mode 1): one vector store
+            // when the four pixels are in the slice and the row is 16-byte aligned
+            if (dst) {
+                const size_t oidx = (size_t)(j - 1) * plane + (size_t)y * W + x0 + lcol;
+                if ((W & 3) == 0 && x0 + lcol + 3 < W) {
+                    *(float4*)(dst + oidx) = make_float4(outv[0], outv[1], outv[2], outv[3]);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        if (x0 + lcol + p < W) dst[oidx + p] = outv[p];
+                }
             }
         }
+        loss += (double)loss4;
+        if (more) loo_commit(nx, V.scale, buf(j + 2), tid);  // buffer of slice j - 2: read last by step j - 1
+        nx = nx2;
+        __syncthreads();
     }
     // loss: warp (FP64) -> block -> volume accumulator
-    double loss = (double)loss4;
     for (int o = 16; o; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
     if (lane == 0) sl[warp] = loss;
     if (mode == 1 && V.cint >= 0) {
@@ -629,7 +656,6 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
         }
     }
     __syncthreads();
-    const int rep = (int)(blockIdx.x % KRIG_LOO_REP);
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += sl[w];
@@ -637,6 +663,7 @@ __device__ void loo_residual_tile(const KrigLaunch& P, int v, int j, int x0, int
     }
     if (mode == 1 && V.cint >= 0 && tid < NO && sgo[tid] != 0.f)
         atomicAdd((double*)(P.ws + V.lorb_off) + rep * KRIG_NORB + tid, (double)sgo[tid]);
+    __syncthreads();  // the next item overwrites the buffers, the weights and sgo
 }
 
 // ---------------------------------------------------------------------------
@@ -717,22 +744,26 @@ __device__ void loo_border_block(const KrigLaunch& P, int64_t b, float* sm)
 // One instance per half-width r (the tap arrays set the register budget);
 // blocks of volumes with another r leave at once.
 template <int R>
-__global__ void __launch_bounds__(256, R == 2 ? 3 : 4) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
+__global__ void __launch_bounds__(256, 2) k_loo_residual(const __grid_constant__ KrigLaunch P, int mode)
 {
     extern __shared__ __align__(16) float lsm[];
     asm volatile("griddepcontrol.launch_dependents;");
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the class weights of this pass
-    const int64_t it = blockIdx.x;
-    int v = 0;
-    for (int u = 1; u < P.n_vols; ++u)
-        if (P.vol[u].loo_item_begin <= it) v = u;
-    const KrigVol& V = P.vol[v];
-    const int64_t local = it - V.loo_item_begin;
-    const int tiles = V.tiles_x * V.tiles_y;
-    const int j = 1 + (int)(local / tiles);
-    const int tile = (int)(local % tiles);
-    const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
-    if (V.r == R) loo_residual_tile<R>(P, v, j, x0, y0, mode, lsm);
+    // a grid of resident blocks walks the chain items (it = blockIdx.x mod gridDim.x)
+    for (int64_t it = blockIdx.x; it < P.n_loo_items; it += gridDim.x) {
+        int v = 0;
+        for (int u = 1; u < P.n_vols; ++u)
+            if (P.vol[u].loo_item_begin <= it) v = u;
+        const KrigVol& V = P.vol[v];
+        if (V.r != R) continue;
+        const int64_t local = it - V.loo_item_begin;
+        const int tiles = V.tiles_x * V.tiles_y;
+        const int chunk = (int)(local / tiles);
+        const int tile = (int)(local % tiles);
+        const int x0 = (tile % V.tiles_x) * LOO_TX, y0 = (tile / V.tiles_x) * LOO_TY;
+        const int ja = 1 + chunk * KRIG_LOO_CHAIN, jb = min(ja + KRIG_LOO_CHAIN, V.n - 1);
+        loo_residual_chain<R>(P, v, ja, jb, x0, y0, mode, (int)(it % KRIG_LOO_REP), lsm);
+    }
     if (mode != 0) return;
     // forward: the last block of the launch turns the loss sums of the volumes
     // with this r into their losses (thread 0 of every block made its loss
@@ -895,8 +926,7 @@ static size_t loo_smem(const KrigLaunch& L, int adjoint)
         const int rows = LOO_TY + 2 * r;
         const int ntap = 2 * (2 * r + 1) * (2 * r + 1);
         const size_t wcap = (size_t)loo_wo_off(25 * ntap) + 8;  // weights + orbit weights
-        size_t b = adjoint ? ((size_t)2 * rows * LOO_SP + wcap) * 4
-                           : ((size_t)2 * rows * LOO_SP + LOO_TY * LOO_SP + wcap + 8) * 4 + 8 * 8;
+        size_t b = adjoint ? ((size_t)2 * rows * LOO_SP + wcap) * 4 : ((size_t)4 * rows * LOO_SP + wcap + 8) * 4 + 8 * 8;
         if (b > m) m = b;
     }
     return m;
@@ -935,12 +965,14 @@ int krig_launch_loo(const KrigLaunch& L, int backward, int want_grad_slices, int
     bool has_r[KRIG_RMAX + 1] = {};
     for (int v = 0; v < L.n_vols; ++v) has_r[L.vol[v].r] = true;
     const size_t s1 = loo_smem(L, 0);
+    // resident blocks of the residual kernel: two per SM (its launch bounds)
+    const unsigned g1 = (unsigned)std::min<int64_t>(L.n_loo_items, (int64_t)2 * krig_device_sm_count());
     for (int r = 0; r <= KRIG_RMAX; ++r) {
         if (!has_r[r]) continue;
         const int mode = backward ? 1 : 0;
-        if (r == 0) e = loo_launch(true, k_loo_residual<0>, (unsigned)L.n_loo_items, s1, st, L, mode);
-        else if (r == 1) e = loo_launch(true, k_loo_residual<1>, (unsigned)L.n_loo_items, s1, st, L, mode);
-        else e = loo_launch(true, k_loo_residual<2>, (unsigned)L.n_loo_items, s1, st, L, mode);
+        if (r == 0) e = loo_launch(true, k_loo_residual<0>, g1, s1, st, L, mode);
+        else if (r == 1) e = loo_launch(true, k_loo_residual<1>, g1, s1, st, L, mode);
+        else e = loo_launch(true, k_loo_residual<2>, g1, s1, st, L, mode);
         if (e != cudaSuccess) return (int)e;
     }
     if (!backward) return 0;
