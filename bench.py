@@ -39,7 +39,7 @@ TOL_GRAD = 1e-4             # normwise, per tensor
 # kernel, from the ncu capture summarised in profiles/ (None until captured, and again
 # whenever the kernel changes).
 NCU_TRAFFIC = {
-    "batch": None,
+    "batch": 611489280,  # schedule 16 gaps per item, 2 blocks per SM (the autotuner's choice may differ)
     "brain": None,
     "spine": None,
 }
@@ -523,6 +523,8 @@ def main():
     ap.add_argument("--results", default=None, help="also append the JSON line to this JSON-lines file")
     ap.add_argument("--schedule", default=None,
                     help="CHUNK,BLOCKS_PER_SM: set the DS schedule instead of autotuning (profiling one fixed launch)")
+    ap.add_argument("--loo-workload", default="spine", choices=["spine", "brain"],
+                    help="stack of the --section loo measurement")
     ap.add_argument("--section", default=None, choices=["uk", "mc", "sim", "loo", "variogram"],
                     help="run only one of the lines beside the headline and print it (a profiling mode; "
                          "not the benchmark's result line)")
@@ -553,7 +555,8 @@ def main():
     extra = {}
     if args.section:
         fn = {"uk": time_uk, "mc": time_mc, "sim": similarity_table,
-              "loo": lambda a, d, s_, f, with_oracle: time_loo(a, d, s_, f, None, with_oracle=with_oracle),
+              "loo": lambda a, d, s_, f, with_oracle: time_loo(a, d, s_, f, None, with_oracle=with_oracle,
+                                                                workload=a.loo_workload),
               "variogram": lambda a, d, s_, f, with_oracle: time_variogram(a, d, s_, f)}[args.section]
         print(json.dumps({"section": args.section, "result": fn(args, dev, stream, flush, with_oracle=not args.no_cpu)}))
         return
@@ -606,6 +609,7 @@ def main():
             extra[key] = r2
         if not args.no_loo:
             extra["fwd_bwd"] = time_loo(args, dev, stream, flush, spine_fit, with_oracle=not args.no_cpu)
+            extra["fwd_bwd_brain"] = time_loo(args, dev, stream, flush, None, with_oracle=False, workload="brain")
         if not args.no_variogram:
             extra["empirical_variogram"] = time_variogram(args, dev, stream, flush)
         if not args.no_downstream:
@@ -660,12 +664,12 @@ def workload_config(vols):
                                        "model": v.model} for v in vols]}
 
 
-def time_loo(args, dev, stream, flush, spine_fit, with_oracle=True):
-    """Leave-one-slice-out forward + backward on the spine stack (gradients w.r.t. every slice voxel and
-    the variogram), replayed as a CUDA graph; gradients compared with the FP64 oracle's."""
+def time_loo(args, dev, stream, flush, spine_fit, with_oracle=True, workload="spine"):
+    """Leave-one-slice-out forward + backward on the spine (or brain) stack (gradients w.r.t. every slice
+    voxel and the variogram), replayed as a CUDA graph; gradients compared with the FP64 oracle's."""
     import torch
     from paper_2303_09523_gb300 import binding, phantoms
-    vol = phantoms.spine()
+    vol = phantoms.brain() if workload == "brain" else phantoms.spine()
     theta = dict(model="spherical", nugget=0.0, sill=vol.sill, range=8.0)
     if spine_fit is not None:
         theta.update(nugget=spine_fit["theta"][0], sill=spine_fit["theta"][1], range=spine_fit["theta"][2])
@@ -708,7 +712,16 @@ def time_loo(args, dev, stream, flush, spine_fit, with_oracle=True):
     plan.device_status(stream)
     plan.close()
     nvox = (vol.n - 2) * vol.H * vol.W
+    # algorithmic bytes of one forward + backward: the slices read by both passes, the
+    # residuals written and read back, dL/dS written
+    plane = vol.H * vol.W
+    abytes = (2 * vol.n * plane * s_dev.element_size() + 2 * (vol.n - 2) * plane * 4 + vol.n * plane * 4)
+    peak, kind = _peaks()
     out = {"value": nvox / (ms * 1e-3), "unit": "LOO-predicted voxels/s (forward + backward)", "ms_per_step": ms,
+           "roofline": {"bound": "hbm", "achieved": abytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": abytes / (ms * 1e-3) / 1e9 / peak, "traffic": None, "algorithmic_bytes": abytes,
+                        "scope": "whole forward + backward step (six launches)",
+                        "peak_source": kind + " hbm_gbs"},
            "replay": "CUDA graph of loo_forward + backward", "workload": vol.name + " (leave-one-slice-out)",
            "voxels_per_step": nvox, "variogram": theta, "loss": float(loss.item()),
            "grad_theta": [float(x) for x in gp.cpu()]}
