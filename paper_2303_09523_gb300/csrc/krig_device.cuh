@@ -526,3 +526,74 @@ __device__ __forceinline__ bool ds_warp_gj(ZSmem& S, int z, int n, int lane)
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Packed pixel pairs: one quantity at two adjacent pixels as one value (FP32: a
+// 64-bit register pair and the f32x2 instructions, each half rounding as the
+// scalar instruction; FP64: two doubles).  Stencils over D4 orbit sums use them
+// so that their arithmetic needs no operand shuffling.
+// ---------------------------------------------------------------------------
+// Two floats as one 64-bit register pair and back (operands of the packed
+// f32x2 instructions).
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+
+
+// One quantity at two adjacent pixels.
+template <typename TC> struct Px2;
+template <> struct Px2<float> {
+    unsigned long long v;
+    __device__ __forceinline__ static Px2 of(float a, float b) { return {pk2(a, b)}; }
+    __device__ __forceinline__ static Px2 zero() { return {0ull}; }
+    __device__ __forceinline__ float x() const { float a, b; upk2(v, a, b); return a; }
+    __device__ __forceinline__ float y() const { float a, b; upk2(v, a, b); return b; }
+};
+template <> struct Px2<double> {
+    double a, b;
+    __device__ __forceinline__ static Px2 of(double x, double y) { return {x, y}; }
+    __device__ __forceinline__ static Px2 zero() { return {0.0, 0.0}; }
+    __device__ __forceinline__ double x() const { return a; }
+    __device__ __forceinline__ double y() const { return b; }
+};
+__device__ __forceinline__ Px2<float> operator+(Px2<float> p, Px2<float> q)
+{
+    Px2<float> r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(p.v), "l"(q.v));
+    return r;
+}
+__device__ __forceinline__ Px2<double> operator+(Px2<double> p, Px2<double> q) { return {p.a + q.a, p.b + q.b}; }
+// acc += w * z, half by half
+__device__ __forceinline__ void px_fma(Px2<float>& acc, Px2<float> w, Px2<float> z)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc.v) : "l"(w.v), "l"(z.v));
+}
+__device__ __forceinline__ void px_fma(Px2<double>& acc, Px2<double> w, Px2<double> z)
+{
+    acc.a = fma(w.a, z.a, acc.a);
+    acc.b = fma(w.b, z.b, acc.b);
+}
+// A weight of the shared-memory table as the pair (w, w): FP32 tables hold the
+// pair already, FP64 tables the value.
+__device__ __forceinline__ Px2<float> px_w(unsigned long long w) { return {w}; }
+__device__ __forceinline__ Px2<double> px_w(double w) { return {w, w}; }
+
+// Pixel pair k (columns m = 4 + 2k, m + 1) of a row of pairs: the values
+// themselves, c[m - 1] + c[m + 1] (shift 1) and c[m - 2] + c[m + 2] (shift 2).
+template <typename TC>
+__device__ __forceinline__ Px2<TC> px_s1(const Px2<TC> (&c)[6], int k)
+{
+    const int h = 2 + k;  // pair index of column m
+    return Px2<TC>::of(c[h - 1].y() + c[h].y(), c[h].x() + c[h + 1].x());
+}
+template <typename TC>
+__device__ __forceinline__ Px2<TC> px_s2(const Px2<TC> (&c)[6], int k)
+{
+    return c[1 + k] + c[3 + k];
+}
