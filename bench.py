@@ -54,6 +54,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+_ALU = {}
+
+
+def _alu_peak(fp64):
+    """FP32 / FP64 FMA throughput of this GPU in GFLOP/s (the library's FMA microbenchmark), once."""
+    from paper_2303_09523_gb300 import binding
+    if fp64 not in _ALU:
+        _ALU[fp64] = binding.measure_fma_peak(fp64)
+    return _ALU[fp64]
+
+
 def workload(name):
     """The volumes of a workload (a list) and its name."""
     from paper_2303_09523_gb300 import phantoms
@@ -781,8 +792,18 @@ def time_uk(args, dev, stream, flush, with_oracle=True):
         torch.cuda.synchronize()
         plan.device_status()
         ms = _graph_time(g.replay, max(5, min(args.steps, 50)), flush, stream)
+        pts = 4 * (2 * vol.half_w + 1) ** 2
+        flops = 2.0 * pts * vol.n_missing  # the weighted sums over the 4-slab neighbourhood
+        abytes = vol.n * vol.H * vol.W * t.element_size() + vol.n_out * vol.H * vol.W * out.element_size()
+        peak = _alu_peak(False)
+        hbm, kind = _peaks()
         r = {"value": vol.n_missing / (ms * 1e-3), "unit": "voxels/s", "ms_per_step": ms, "workload": vol.name,
-             "drift": "1, x, y, z", "slabs": 4, "points_per_voxel": 4 * (2 * vol.half_w + 1) ** 2}
+             "drift": "1, x, y, z", "slabs": 4, "points_per_voxel": pts,
+             "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GFLOP/s",
+                          "frac": flops / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                          "scope": "whole step (FP64 class solve + stencil); 2 flops per point and interpolated voxel",
+                          "peak_source": "krig_measure_fma_peak (FP32 FMA microbenchmark)",
+                          "hbm_frac": abytes / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": abytes}}
         if with_oracle:
             import oracle
             rng = np.random.default_rng(21)
@@ -868,7 +889,14 @@ def similarity_table(args, dev, stream, flush, with_oracle=True):
         ms = _graph_time(lambda: binding.similarity(G, R, stream=stream), 5, flush, stream)
         mh = m.cpu().numpy()
         varied = G.reshape(len(miss), -1).std(dim=1).cpu().numpy() > 0
+        # the pixel pairs are read by the moments pass and again by the histogram pass (4 + 4 bytes each)
+        sbytes = 2 * 2 * G.numel() * 4
+        hbm, kind = _peaks()
         row = {"images": len(miss), "ms_per_call": ms, "workload": vol.name,
+               "roofline": {"bound": "hbm", "achieved": sbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": sbytes / (ms * 1e-3) / 1e9 / hbm, "traffic": None, "algorithmic_bytes": sbytes,
+                            "scope": "the four similarity kernels (FP64-pipe bound: sums and logarithms in FP64)",
+                            "peak_source": kind + " hbm_gbs"},
                "mean_rmse": float(mh[:, 0].mean()), "mean_mi": float(mh[:, 1].mean()),
                "mean_mi_gg": float(mh[:, 2].mean()), "mean_ed": float(mh[:, 3].mean()),
                "mean_ssim_anatomy_slices": float(mh[varied, 4].mean()) if varied.any() else None}
@@ -937,8 +965,13 @@ def time_variogram(args, dev, stream, flush, max_lag=8):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     pairs = int(counts.sum())
+    peak = _alu_peak(False)
+    gf = 2.0 * pairs / (ms * 1e-3) / 1e9  # a subtract and a fused multiply-add per voxel pair
     out = {"value": pairs / (ms * 1e-3), "unit": "voxel pairs/s", "ms_per_call": ms, "max_lag": max_lag,
-           "lag_vectors": int(counts.size), "pairs_per_call": pairs, "workload": vol.name}
+           "lag_vectors": int(counts.size), "pairs_per_call": pairs, "workload": vol.name,
+           "roofline": {"bound": "alu", "achieved": gf, "peak": peak, "unit": "GFLOP/s", "frac": gf / peak,
+                        "traffic": None, "scope": "k_emp_variogram; 2 flops per voxel pair",
+                        "peak_source": "krig_measure_fma_peak (FP32 FMA microbenchmark)"}}
     # the fit uses the widest lags the kernel stages (16 pixels: distance classes to about 23 voxels)
     sums16, counts16 = binding.empirical_variogram(s_dev, 16, in_scale=vol.in_scale, stream=stream)
     out["fit"] = variogram_fits(sums16.cpu().numpy(), counts16, vol)

@@ -273,19 +273,35 @@ __device__ __forceinline__ float uk_cvt(float x, float) { return x; }
 __device__ __forceinline__ double uk_cvt(double x, float) { return x; }
 __device__ __forceinline__ float uk_cvt(uint16_t u, float) { return (float)u; }
 
-template <typename TI, int R>
+// D4 orbit of tap (dx, dy): {same max(|dx|,|dy|), min(|dx|,|dy|)}, numbered a (a + 1) / 2 + b.
+__host__ __device__ constexpr int uk_orbit(int dx, int dy)
+{
+    const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+    const int a = ax > ay ? ax : ay, b = ax > ay ? ay : ax;
+    return a * (a + 1) / 2 + b;
+}
+
+// One block per (volume, gap j, 32 x 16 tile): the gap's slabs staged in shared
+// memory, each thread two pixels, every target t of the gap.  The interior class
+// is invariant under the in-plane symmetries of the square (its window is full
+// and the drift space {1, x, y, z} is mapped onto itself by them), so its
+// weights are constant on each D4 orbit of every slab: interior pixels take
+// orbit sums per slab and one weight per (slab, orbit, t), the orbit's member
+// (dx, dy) = (a, b) of the solved row; the other classes take their full rows.
+template <typename TI, int R, int GM1>
 __device__ __forceinline__ void uk_apply_block(const KrigLaunch& P, int v, int j, int tile, unsigned char* smem)
 {
     typedef typename UkT<TI>::TC TC;
     typedef typename UkT<TI>::TO TO;
     constexpr int N2R = 2 * R + 1, TW = KRIG_UK_TX + 2 * R, TH = KRIG_UK_TY + 2 * R;
+    constexpr int NO = (R + 1) * (R + 2) / 2;
     const KrigVol& V = P.vol[v];
-    const int slabs = P.uk_slabs, H = V.H, W = V.W, g = V.g, G1 = g - 1, n = V.n;
+    const int slabs = P.uk_slabs, H = V.H, W = V.W, g = V.g, n = V.n;
     const int x0 = (tile % V.uk_tiles_x) * KRIG_UK_TX, y0 = (tile / V.uk_tiles_x) * KRIG_UK_TY;
     const int64_t plane = (int64_t)H * W;
     const TI* in = (const TI*)P.in[v];
     TC* tiles = (TC*)smem;                                  // [slabs][TH][TW]
-    TC* wint = tiles + UK_MAXS * TH * TW;                   // interior class row [slabs][N2R][N2R][8]
+    TC* wint = tiles + UK_MAXS * TH * TW;                   // interior weights per orbit [slabs][NO][8]
     const int pat = slabs == 4 ? ((j == 0 ? 1 : 0) | (j + 2 > n - 1 ? 2 : 0)) : 0;
     const int ntap = slabs * N2R * N2R;
     for (int e = threadIdx.x; e < slabs * TH * TW; e += UK_THREADS) {
@@ -300,8 +316,13 @@ __device__ __forceinline__ void uk_apply_block(const KrigLaunch& P, int v, int j
     const TC* wtab = (const TC*)(P.ws + V.uk_wtab_off);
     const float* vtab = (const float*)(P.ws + V.uk_vtab_off);
     if (V.cint >= 0)
-        for (int e = threadIdx.x; e < ntap * KRIG_TSLOTS; e += UK_THREADS)
-            wint[e] = wtab[(cls_base + V.cint) * ntap * KRIG_TSLOTS + e];
+        for (int e = threadIdx.x; e < slabs * NO * KRIG_TSLOTS; e += UK_THREADS) {
+            const int t = e % KRIG_TSLOTS, o = (e / KRIG_TSLOTS) % NO, s = e / (KRIG_TSLOTS * NO);
+            int a = 0;
+            while ((a + 1) * (a + 2) / 2 <= o) ++a;
+            const int b = o - a * (a + 1) / 2;  // member (dx, dy) = (a, b)
+            wint[e] = wtab[(cls_base + V.cint) * ntap * KRIG_TSLOTS + ((s * N2R + (b + R)) * N2R + (a + R)) * KRIG_TSLOTS + t];
+        }
     __syncthreads();
     const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 2;
     const int y = y0 + row;
@@ -322,29 +343,66 @@ __device__ __forceinline__ void uk_apply_block(const KrigLaunch& P, int v, int j
             out[(int64_t)(j + 1) * g * plane + pix] = (TO)(sizeof(TI) == 2 ? __fmul_rn((float)kl, V.scale) : kl);
             if (var) var[(int64_t)(j + 1) * g * plane + pix] = 0.0f;
         }
-        if (G1 < 1) continue;
-        const int cy = V.ymap[krig_slot(y, H, R)], cx = V.xmap[krig_slot(x, W, R)];
-        const int64_t cls = cls_base + (int64_t)cy * V.ncx + cx;
-        const TC* w = (cy * V.ncx + cx == V.cint) ? wint : wtab + cls * ntap * KRIG_TSLOTS;
-        TC acc[KRIG_GMAX - 1];
+        if constexpr (GM1 > 0) {
+            const int cy = V.ymap[krig_slot(y, H, R)], cx = V.xmap[krig_slot(x, W, R)];
+            const int64_t cls = cls_base + (int64_t)cy * V.ncx + cx;
+            TC acc[GM1];
 #pragma unroll
-        for (int t = 0; t < KRIG_GMAX - 1; ++t) acc[t] = TC(0);
-        for (int s = 0; s < slabs; ++s)
+            for (int t = 0; t < GM1; ++t) acc[t] = TC(0);
+            if (cy * V.ncx + cx == V.cint) {
 #pragma unroll
-            for (int dy = 0; dy < N2R; ++dy)
+                for (int s = 0; s < UK_MAXS; ++s) {
+                    if (s >= slabs) break;
+                    TC orb[NO];
 #pragma unroll
-                for (int dx = 0; dx < N2R; ++dx) {
-                    const TC z = tiles[(s * TH + row + dy) * TW + col + q + dx];
-                    const TC* wr = w + ((s * N2R + dy) * N2R + dx) * KRIG_TSLOTS;
+                    for (int o = 0; o < NO; ++o) orb[o] = TC(0);
 #pragma unroll
-                    for (int t = 0; t < KRIG_GMAX - 1; ++t)
-                        if (t < G1) acc[t] = fma(wr[t], z, acc[t]);
+                    for (int dy = 0; dy < N2R; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < N2R; ++dx)
+                            orb[uk_orbit(dx - R, dy - R)] += tiles[(s * TH + row + dy) * TW + col + q + dx];
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) {
+                        const TC* wr = wint + (s * NO + o) * KRIG_TSLOTS;
+#pragma unroll
+                        for (int t = 0; t < GM1; ++t) acc[t] = fma(wr[t], orb[o], acc[t]);
+                    }
                 }
-        const float* vr = vtab + cls * KRIG_TSLOTS;
-        for (int t = 0; t < G1; ++t) {
-            out[((int64_t)j * g + t + 1) * plane + pix] = (TO)acc[t];
-            if (var) var[((int64_t)j * g + t + 1) * plane + pix] = vr[t];
+            } else {
+                const TC* w = wtab + cls * ntap * KRIG_TSLOTS;
+                for (int s = 0; s < slabs; ++s)
+#pragma unroll
+                    for (int dy = 0; dy < N2R; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < N2R; ++dx) {
+                            const TC z = tiles[(s * TH + row + dy) * TW + col + q + dx];
+                            const TC* wr = w + ((s * N2R + dy) * N2R + dx) * KRIG_TSLOTS;
+#pragma unroll
+                            for (int t = 0; t < GM1; ++t) acc[t] = fma(wr[t], z, acc[t]);
+                        }
+            }
+            const float* vr = vtab + cls * KRIG_TSLOTS;
+#pragma unroll
+            for (int t = 0; t < GM1; ++t) {
+                out[((int64_t)j * g + t + 1) * plane + pix] = (TO)acc[t];
+                if (var) var[((int64_t)j * g + t + 1) * plane + pix] = vr[t];
+            }
         }
+    }
+}
+
+template <typename TI, int R>
+__device__ __forceinline__ void uk_apply_g(const KrigLaunch& P, int v, int g, int j, int tile, unsigned char* smem)
+{
+    switch (g) {
+    case 1: uk_apply_block<TI, R, 0>(P, v, j, tile, smem); break;
+    case 2: uk_apply_block<TI, R, 1>(P, v, j, tile, smem); break;
+    case 3: uk_apply_block<TI, R, 2>(P, v, j, tile, smem); break;
+    case 4: uk_apply_block<TI, R, 3>(P, v, j, tile, smem); break;
+    case 5: uk_apply_block<TI, R, 4>(P, v, j, tile, smem); break;
+    case 6: uk_apply_block<TI, R, 5>(P, v, j, tile, smem); break;
+    case 7: uk_apply_block<TI, R, 6>(P, v, j, tile, smem); break;
+    default: uk_apply_block<TI, R, 7>(P, v, j, tile, smem); break;
     }
 }
 
@@ -363,9 +421,9 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_apply(const __grid_constant__
     const int local = (int)(it - V.uk_item_begin);
     const int j = local / tiles, tile = local % tiles;
     switch (V.r) {
-    case 0: uk_apply_block<TI, 0>(P, v, j, tile, uk_smem); break;
-    case 1: uk_apply_block<TI, 1>(P, v, j, tile, uk_smem); break;
-    default: uk_apply_block<TI, 2>(P, v, j, tile, uk_smem); break;
+    case 0: uk_apply_g<TI, 0>(P, v, V.g, j, tile, uk_smem); break;
+    case 1: uk_apply_g<TI, 1>(P, v, V.g, j, tile, uk_smem); break;
+    default: uk_apply_g<TI, 2>(P, v, V.g, j, tile, uk_smem); break;
     }
 }
 
