@@ -51,6 +51,8 @@ struct UkSolveSmem {
     double S[UK_PMAX * UK_PMAX];
     double lam[KRIG_GMAX - 1][UK_PMAX];
     double var[KRIG_GMAX - 1];
+    // covariance at every distinct lag between two points: [slab distance][|dy|][|dx|]
+    double lag[UK_MAXS][2 * KRIG_RMAX + 1][2 * KRIG_RMAX + 1];
     int tap[UK_KMAX];             // (s * n2r + dy + r) * n2r + dx + r in the full window
     int ok;
 };
@@ -96,12 +98,21 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
     uk_sync();
     const int K = M.ok;
     const int NR = G1 + p;
-    // C, the right-hand sides c0(t) and the drift columns F
+    // C from one covariance evaluation per distinct lag (slab distance, |dy|, |dx|):
+    // the same squared lag, hence the same value, as an evaluation per entry
+    for (int e = tid; e < UK_MAXS * n2r * n2r; e += UK_THREADS) {
+        const int ax = e % n2r, ay = (e / n2r) % n2r, ds = e / (n2r * n2r);
+        const double dx = ax, dy = ay, dz = (double)ds * g;
+        M.lag[ds][ay][ax] = krig_cov(vg, dx * dx + dy * dy + dz * dz);
+    }
+    uk_sync();
     for (int e = tid; e < K * K; e += UK_THREADS) {
         const int i = e / K, j = e % K;
-        const double dx = M.pt[i][0] - M.pt[j][0], dy = M.pt[i][1] - M.pt[j][1], dz = M.pt[i][2] - M.pt[j][2];
-        M.A[i * K + j] = krig_cov(vg, dx * dx + dy * dy + dz * dz);
+        const int ax = abs((int)M.pt[i][0] - (int)M.pt[j][0]), ay = abs((int)M.pt[i][1] - (int)M.pt[j][1]);
+        const int ds = abs(M.tap[i] / (n2r * n2r) - M.tap[j] / (n2r * n2r));  // slab distance
+        M.A[i * K + j] = M.lag[ds][ay][ax];
     }
+    // the right-hand sides c0(t) and the drift columns F
     for (int e = tid; e < K * G1; e += UK_THREADS) {
         const int i = e / G1, t = e % G1 + 1;
         const double dz = M.pt[i][2] - t;
