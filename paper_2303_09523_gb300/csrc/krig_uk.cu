@@ -53,6 +53,10 @@ struct UkSolveSmem {
     double var[KRIG_GMAX - 1];
     // covariance at every distinct lag between two points: [slab distance][|dy|][|dx|]
     double lag[UK_MAXS][2 * KRIG_RMAX + 1][2 * KRIG_RMAX + 1];
+    double B[UK_KMAX * UK_NRHS];   // the right-hand sides [c0 | F], kept for the residuals
+    float L[UK_KMAX * UK_KMAX];    // FP32 Cholesky factor of C (lower)
+    float Z[UK_KMAX * UK_NRHS];    // FP32 sweep operand
+    float col[UK_KMAX];            // the current column of the factorisation
     int tap[UK_KMAX];             // (s * n2r + dy + r) * n2r + dx + r in the full window
     int ok;
 };
@@ -128,47 +132,89 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
         M.X[i * UK_NRHS + G1 + k] = f;
     }
     uk_sync();
-    // Cholesky factorisation of C in place (lower triangle), right-looking
+    // C X = [c0 | F] by an FP32 Cholesky factorisation and two refinement steps with
+    // FP64 residuals (FP64 issues at 1/64 of the FP32 rate on this GPU; C stays in
+    // FP64 in A for the residuals)
+    for (int e = tid; e < K * K; e += UK_THREADS) M.L[e] = (float)M.A[e];
+    for (int e = tid; e < K * NR; e += UK_THREADS) {
+        const int i = e / NR, c = e % NR;
+        M.B[i * UK_NRHS + c] = M.X[i * UK_NRHS + c];
+    }
+    uk_sync();
     bool ok = true;
     for (int k = 0; k < K; ++k) {
-        const double d = M.A[k * K + k];
-        if (!(d > 0.0)) {
+        const float d = M.L[k * K + k];
+        if (!(d > 0.0f)) {  // the same value in every thread
             ok = false;
             break;
         }
-        const double l = sqrt(d);
+        const float l = sqrtf(d), il = 1.0f / l;
         uk_sync();
-        for (int i = k + 1 + tid; i < K; i += UK_THREADS) M.A[i * K + k] /= l;
-        if (tid == 0) M.A[k * K + k] = l;
+        for (int i = k + 1 + tid; i < K; i += UK_THREADS) {
+            const float v = M.L[i * K + k] * il;
+            M.L[i * K + k] = v;
+            M.col[i] = v;
+        }
+        if (tid == 0) M.L[k * K + k] = l;
         uk_sync();
-        const int m = K - k - 1;
-        for (int e = tid; e < m * m; e += UK_THREADS) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            if (j <= i) M.A[i * K + j] -= M.A[i * K + k] * M.A[j * K + k];
+        // trailing update of the lower triangle: rows i, columns j <= i (16 x 16 thread grid)
+        for (int i = k + 1 + (tid >> 4); i < K; i += 16) {
+            const float li = M.col[i];
+            for (int j = k + 1 + (tid & 15); j <= i; j += 16) M.L[i * K + j] = fmaf(-li, M.col[j], M.L[i * K + j]);
         }
         uk_sync();
     }
+    // Z <- C^-1 Z by the FP32 factor, every column at once (thread grid: 16 rows x 16 columns)
+    auto sweeps = [&]() {
+        for (int i = 0; i < K; ++i) {
+            if (tid < NR) M.Z[i * UK_NRHS + tid] /= M.L[i * K + i];
+            uk_sync();
+            if ((tid & 15) < NR)
+                for (int k2 = i + 1 + (tid >> 4); k2 < K; k2 += 16)
+                    M.Z[k2 * UK_NRHS + (tid & 15)] =
+                        fmaf(-M.L[k2 * K + i], M.Z[i * UK_NRHS + (tid & 15)], M.Z[k2 * UK_NRHS + (tid & 15)]);
+            uk_sync();
+        }
+        for (int i = K - 1; i >= 0; --i) {
+            if (tid < NR) M.Z[i * UK_NRHS + tid] /= M.L[i * K + i];
+            uk_sync();
+            if ((tid & 15) < NR)
+                for (int k2 = (tid >> 4); k2 < i; k2 += 16)
+                    M.Z[k2 * UK_NRHS + (tid & 15)] =
+                        fmaf(-M.L[i * K + k2], M.Z[i * UK_NRHS + (tid & 15)], M.Z[k2 * UK_NRHS + (tid & 15)]);
+            uk_sync();
+        }
+    };
     if (!ok) {
         if (tid == 0) krig_set_status(P.status, KRIG_DEV_SINGULAR);
     } else {
-        // C X = [c0 | F]: one warp per column, forward then backward substitution
-        for (int col = warp; col < NR; col += UK_THREADS / 32) {
-            for (int i = 0; i < K; ++i) {
-                double s = 0.0;
-                for (int k = lane; k < i; k += 32) s += M.A[i * K + k] * M.X[k * UK_NRHS + col];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) M.X[i * UK_NRHS + col] = (M.X[i * UK_NRHS + col] - s) / M.A[i * K + i];
-                __syncwarp();
-            }
-            for (int i = K - 1; i >= 0; --i) {
-                double s = 0.0;
-                for (int k = i + 1 + lane; k < K; k += 32) s += M.A[k * K + i] * M.X[k * UK_NRHS + col];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) M.X[i * UK_NRHS + col] = (M.X[i * UK_NRHS + col] - s) / M.A[i * K + i];
-                __syncwarp();
-            }
+        for (int e = tid; e < K * NR; e += UK_THREADS) {
+            const int i = e / NR, c = e % NR;
+            M.Z[i * UK_NRHS + c] = (float)M.B[i * UK_NRHS + c];
         }
         uk_sync();
+        sweeps();
+        for (int e = tid; e < K * NR; e += UK_THREADS) {
+            const int i = e / NR, c = e % NR;
+            M.X[i * UK_NRHS + c] = (double)M.Z[i * UK_NRHS + c];
+        }
+        uk_sync();
+        for (int it = 0; it < 2; ++it) {
+            // R = [c0 | F] - C X in FP64, then X += C^-1 R in FP32
+            for (int e = tid; e < K * NR; e += UK_THREADS) {
+                const int i = e / NR, c = e % NR;
+                double acc = M.B[i * UK_NRHS + c];
+                for (int j = 0; j < K; ++j) acc = fma(-M.A[i * K + j], M.X[j * UK_NRHS + c], acc);
+                M.Z[i * UK_NRHS + c] = (float)acc;
+            }
+            uk_sync();
+            sweeps();
+            for (int e = tid; e < K * NR; e += UK_THREADS) {
+                const int i = e / NR, c = e % NR;
+                M.X[i * UK_NRHS + c] += (double)M.Z[i * UK_NRHS + c];
+            }
+            uk_sync();
+        }
         // S = F' C^-1 F, and per target the multipliers: S lambda = F' C^-1 c0 - f0
         if (tid < p * p) {
             const int a = tid / p, b = tid % p;
