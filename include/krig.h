@@ -73,8 +73,10 @@ typedef enum { KRIG_F64 = 0, KRIG_F32 = 1, KRIG_U16 = 2 } krig_dtype;
  *   P64: one FP64 system per missing voxel (the plain reference form).
  *   PMX: one system per missing voxel, FP32 factorisation plus one FP64
  *        iterative-refinement step.
- *   DS : one FP64 system per neighbourhood geometry class, applied to every
- *        voxel of that class as an FP32 stencil (FP64 for KRIG_F64 input).
+ *   DS : one system per neighbourhood geometry class (FP32 factorisation,
+ *        one refinement step with a float-float residual; FP64 throughout
+ *        with KRIG_FLAG_DS_FP64_SOLVE), applied to every voxel of that class
+ *        as an FP32 stencil (FP64 for KRIG_F64 input).
  *        A voxel's system depends only on t and on how its window is
  *        truncated at the border, so the solutions repeat across voxels. */
 typedef enum { KRIG_FORM_P64 = 0, KRIG_FORM_PMX = 1, KRIG_FORM_DS = 2 } krig_form;
@@ -103,7 +105,8 @@ typedef struct {
 
 /* Plan flags.
  *   KRIG_FLAG_DS_FP64_SOLVE: DS form only -- factorise the class systems in
- *   FP64 instead of FP32 followed by one FP64 iterative-refinement step. */
+ *   FP64 instead of FP32 followed by one refinement step whose residual is
+ *   formed in float-float (about 48 significant bits). */
 #define KRIG_FLAG_DS_FP64_SOLVE 0x1u
 /*   KRIG_FLAG_FAULT_TIMEOUT: test only -- the DS stencil kernel waits once on a
  *   barrier that nothing completes, so its bounded wait gives up and the call's
@@ -123,8 +126,9 @@ typedef struct {
  *                          as 4 slices x the in-plane window), instead of the
  *                          bracketing pair j, j+1.
  *   Either drift flag, or KRIG_FLAG_SLABS4 alone (constant drift: ordinary
- *   kriging on four slices), selects the universal-kriging path: one FP64
- *   class solve per geometry class (truncation, and which outer slices exist)
+ *   kriging on four slices), selects the universal-kriging path: one class
+ *   solve per geometry class (truncation, and which outer slices exist; FP32
+ *   Cholesky factorisation, two refinement steps with FP64 residuals)
  *   with all targets t of a gap, then the stencil with each class's weights.
  *   The kriging variance is w'gamma0 + mu'f0.  Not combinable with
  *   KRIG_FLAG_LOO, KRIG_FLAG_DS_FP64_SOLVE or KRIG_FLAG_FAULT_TIMEOUT. */
