@@ -14,8 +14,8 @@
 // and, with four slabs, on which of the outer slices exist (the first gap has
 // none below, the last none above).  In coordinates relative to the gap's lower
 // known slice the point-to-point covariances and the drift rows do not depend
-// on t either, so each class is one FP64 Cholesky factorisation shared by all
-// g-1 targets (the drift basis {1, x, y, z - t} of the target-centred system
+// on t either, so each class is one Cholesky factorisation shared by all g-1
+// targets (FP32 factor, two refinement steps with FP64 residuals) (the drift basis {1, x, y, z - t} of the target-centred system
 // and {1, x, y, z} span the same functions, so the weights are the same).
 //
 // Covariance form (C(h) = nugget + sill - gamma(h), SPD for a valid model):
@@ -318,10 +318,11 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
 // ---------------------------------------------------------------------------
 // Stencil apply: one block per (volume, gap, 32 x 16 tile).  The gap's slabs
 // (tile plus halo, zeros outside the stack) are staged in shared memory; each
-// thread computes two pixels of one row, every target t of the gap, through
-// the full weight row of the pixel's class (the interior class's row staged in
-// shared memory, border classes read through L1).  The block also copies the
-// gap's lower known slice (and the stack's last one) to the output.
+// thread computes two pixels of one row, every target t of the gap: interior
+// pixels through per-slab D4 orbit sums and the interior class's orbit weights
+// (staged in shared memory), border pixels through the full weight row of their
+// class (read through L1).  The block also copies the gap's lower known slice
+// (and the stack's last one) to the output.
 // ---------------------------------------------------------------------------
 template <typename TI> struct UkT { typedef float TC; typedef float TO; };
 template <> struct UkT<double> { typedef double TC; typedef double TO; };
