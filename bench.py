@@ -784,7 +784,7 @@ def _graph_time(fn, steps, flush, stream):
 
 def time_uk(args, dev, stream, flush, with_oracle=True):
     """Universal kriging (drift {1, x, y, z}, four known slices) on the spine and brain stacks:
-    FP64 class solve + stencil replayed as a CUDA graph, error against orc_uk_voxels on a sample."""
+    class solve + stencil replayed as a CUDA graph, error against orc_uk_voxels on a sample."""
     import torch
     from paper_2303_09523_gb300 import binding, phantoms
     res = {}
@@ -810,7 +810,7 @@ def time_uk(args, dev, stream, flush, with_oracle=True):
              "drift": "1, x, y, z", "slabs": 4, "points_per_voxel": pts,
              "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GFLOP/s",
                           "frac": flops / (ms * 1e-3) / 1e9 / peak, "traffic": None,
-                          "scope": "whole step (FP64 class solve + stencil); 2 flops per point and interpolated voxel",
+                          "scope": "whole step (class solve + stencil); 2 flops per point and interpolated voxel",
                           "peak_source": "krig_measure_fma_peak (FP32 FMA microbenchmark)",
                           "hbm_frac": abytes / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": abytes}}
         if with_oracle:

@@ -128,7 +128,7 @@ typedef struct {
  *   Either drift flag, or KRIG_FLAG_SLABS4 alone (constant drift: ordinary
  *   kriging on four slices), selects the universal-kriging path: one class
  *   solve per geometry class (truncation, and which outer slices exist; FP32
- *   Cholesky factorisation, two refinement steps with FP64 residuals)
+ *   Cholesky factorisation, two refinement steps with float-float residuals)
  *   with all targets t of a gap, then the stencil with each class's weights.
  *   The kriging variance is w'gamma0 + mu'f0.  Not combinable with
  *   KRIG_FLAG_LOO, KRIG_FLAG_DS_FP64_SOLVE or KRIG_FLAG_FAULT_TIMEOUT. */

@@ -15,7 +15,7 @@
 // none below, the last none above).  In coordinates relative to the gap's lower
 // known slice the point-to-point covariances and the drift rows do not depend
 // on t either, so each class is one Cholesky factorisation shared by all g-1
-// targets (FP32 factor, two refinement steps with FP64 residuals) (the drift basis {1, x, y, z - t} of the target-centred system
+// targets (FP32 factor, two refinement steps with float-float residuals) (the drift basis {1, x, y, z - t} of the target-centred system
 // and {1, x, y, z} span the same functions, so the weights are the same).
 //
 // Covariance form (C(h) = nugget + sill - gamma(h), SPD for a valid model):
@@ -44,7 +44,7 @@ __host__ __device__ inline int uk_slab_dj(int slabs, int s) { return slabs == 4 
 
 // Dynamic shared memory of the class solve.
 struct UkSolveSmem {
-    double A[UK_KMAX * UK_KMAX];  // C, then its Cholesky factor (lower)
+    ff A[UK_KMAX * UK_KMAX];      // C as float-float pairs (for the refinement residuals)
     double X[UK_KMAX * UK_NRHS];  // right-hand sides [i][col], then the solutions
     double c0[UK_KMAX * (KRIG_GMAX - 1)];
     double pt[UK_KMAX][3];
@@ -52,8 +52,9 @@ struct UkSolveSmem {
     double lam[KRIG_GMAX - 1][UK_PMAX];
     double var[KRIG_GMAX - 1];
     // covariance at every distinct lag between two points: [slab distance][|dy|][|dx|]
-    double lag[UK_MAXS][2 * KRIG_RMAX + 1][2 * KRIG_RMAX + 1];
-    double B[UK_KMAX * UK_NRHS];   // the right-hand sides [c0 | F], kept for the residuals
+    ff lag[UK_MAXS][2 * KRIG_RMAX + 1][2 * KRIG_RMAX + 1];
+    ff B[UK_KMAX * UK_NRHS];       // the right-hand sides [c0 | F], kept for the residuals
+    ff Xf[UK_KMAX * UK_NRHS];      // the solution during the refinement
     float L[UK_KMAX * UK_KMAX];    // FP32 Cholesky factor of C (lower)
     float Z[UK_KMAX * UK_NRHS];    // FP32 sweep operand
     float col[UK_KMAX];            // the current column of the factorisation
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
     for (int e = tid; e < UK_MAXS * n2r * n2r; e += UK_THREADS) {
         const int ax = e % n2r, ay = (e / n2r) % n2r, ds = e / (n2r * n2r);
         const double dx = ax, dy = ay, dz = (double)ds * g;
-        M.lag[ds][ay][ax] = krig_cov(vg, dx * dx + dy * dy + dz * dz);
+        M.lag[ds][ay][ax] = ff_from_double(krig_cov(vg, dx * dx + dy * dy + dz * dz));
     }
     uk_sync();
     for (int e = tid; e < K * K; e += UK_THREADS) {
@@ -133,12 +134,12 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
     }
     uk_sync();
     // C X = [c0 | F] by an FP32 Cholesky factorisation and two refinement steps with
-    // FP64 residuals (FP64 issues at 1/64 of the FP32 rate on this GPU; C stays in
-    // FP64 in A for the residuals)
-    for (int e = tid; e < K * K; e += UK_THREADS) M.L[e] = (float)M.A[e];
+    // float-float residuals (FP64 issues at 1/64 of the FP32 rate on this GPU; C
+    // and the right-hand sides are kept as pairs for the residuals)
+    for (int e = tid; e < K * K; e += UK_THREADS) M.L[e] = M.A[e].hi;
     for (int e = tid; e < K * NR; e += UK_THREADS) {
         const int i = e / NR, c = e % NR;
-        M.B[i * UK_NRHS + c] = M.X[i * UK_NRHS + c];
+        M.B[i * UK_NRHS + c] = ff_from_double(M.X[i * UK_NRHS + c]);
     }
     uk_sync();
     bool ok = true;
@@ -190,31 +191,41 @@ __global__ void __launch_bounds__(UK_THREADS) k_uk_solve(const __grid_constant__
     } else {
         for (int e = tid; e < K * NR; e += UK_THREADS) {
             const int i = e / NR, c = e % NR;
-            M.Z[i * UK_NRHS + c] = (float)M.B[i * UK_NRHS + c];
+            M.Z[i * UK_NRHS + c] = M.B[i * UK_NRHS + c].hi;
         }
         uk_sync();
         sweeps();
         for (int e = tid; e < K * NR; e += UK_THREADS) {
             const int i = e / NR, c = e % NR;
-            M.X[i * UK_NRHS + c] = (double)M.Z[i * UK_NRHS + c];
+            M.Xf[i * UK_NRHS + c] = ff_make(M.Z[i * UK_NRHS + c]);
         }
         uk_sync();
         for (int it = 0; it < 2; ++it) {
-            // R = [c0 | F] - C X in FP64, then X += C^-1 R in FP32
+            // R = [c0 | F] - C X compensated (Dot2 over the pairs; the low part of X
+            // enters the compensation), then X += C^-1 R in FP32
             for (int e = tid; e < K * NR; e += UK_THREADS) {
                 const int i = e / NR, c = e % NR;
-                double acc = M.B[i * UK_NRHS + c];
-                for (int j = 0; j < K; ++j) acc = fma(-M.A[i * K + j], M.X[j * UK_NRHS + c], acc);
-                M.Z[i * UK_NRHS + c] = (float)acc;
+                ff_dot acc(M.B[i * UK_NRHS + c]);
+                for (int j = 0; j < K; ++j) {
+                    const ff a = M.A[i * K + j], x = M.Xf[j * UK_NRHS + c];
+                    acc.add(a, -x.hi);
+                    acc.c = __fmaf_rn(-a.hi, x.lo, acc.c);
+                }
+                M.Z[i * UK_NRHS + c] = ff_round(acc.value());
             }
             uk_sync();
             sweeps();
             for (int e = tid; e < K * NR; e += UK_THREADS) {
                 const int i = e / NR, c = e % NR;
-                M.X[i * UK_NRHS + c] += (double)M.Z[i * UK_NRHS + c];
+                M.Xf[i * UK_NRHS + c] = ff_add(M.Xf[i * UK_NRHS + c], ff_make(M.Z[i * UK_NRHS + c]));
             }
             uk_sync();
         }
+        for (int e = tid; e < K * NR; e += UK_THREADS) {
+            const int i = e / NR, c = e % NR;
+            M.X[i * UK_NRHS + c] = ff_to_double(M.Xf[i * UK_NRHS + c]);
+        }
+        uk_sync();
         // S = F' C^-1 F, and per target the multipliers: S lambda = F' C^-1 c0 - f0
         if (tid < p * p) {
             const int a = tid / p, b = tid % p;
